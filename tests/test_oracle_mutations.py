@@ -1,0 +1,109 @@
+"""Planted mistakes: each test swaps one oracle function for a subtly wrong
+version (a sign, a dropped term, a transposed operand, a wrong tie rule) and
+checks that at least one of the oracle's pins then fails.  The mistakes are
+planted in the oracle only, on the CPU."""
+import numpy as np
+import pytest
+
+from oracle import zoom_oracle as O
+from tests import test_golden as TG
+from tests import test_oracle_degrade as TD
+from tests import test_oracle_hash as TH
+from tests import test_oracle_knn_lle as TK
+from tests import test_oracle_recon_bp as TR
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_wrong_bp_sign_is_caught(monkeypatch):
+    # adding the filtered error (the literal sign of Eq. 7) instead of
+    # subtracting it
+    def bp_plus(x, y, s, blur_sigma, iters, sigma_sp, sigma_r, radius):
+        x = np.asarray(x, np.float64).copy()
+        ck = O.spatial_kernel(sigma_sp, radius)
+        box = np.full((2 * radius + 1,) * 2, 1.0 / (2 * radius + 1) ** 2)
+        for _ in range(iters):
+            e = O.degrade(x, s, blur_sigma) - y
+            g = O.window_sum_clamped(np.kron(e, np.ones((s, s))), ck)
+            m = O.window_sum_clamped(x, box)
+            x = x + np.exp(-(x - m) ** 2 / (2 * sigma_r ** 2)) * g
+        return x
+    monkeypatch.setattr(O, "back_project", bp_plus)
+    _fails(TR.test_bp_removes_constant_error_in_one_step, np.random.default_rng(0))
+
+
+def test_blur_on_one_axis_only_is_caught(monkeypatch):
+    def blur_rows_only(x, taps):
+        r = len(taps) // 2
+        h, w = x.shape
+        xp = np.pad(np.asarray(x, np.float64), ((r, r), (0, 0)), mode="edge")
+        return sum(taps[u] * xp[u:u + h] for u in range(len(taps)))
+    monkeypatch.setattr(O, "blur", blur_rows_only)
+    _fails(TD.test_blur_equals_scipy_gaussian_filter, np.random.default_rng(0))
+
+
+def test_decimation_adjoint_without_scale_is_caught(monkeypatch):
+    # D^T spreading each LR value without the 1/s^2 factor of the box mean
+    def adj_unscaled(y, s, sigma, hr_shape):
+        z = np.zeros(hr_shape)
+        h, w = y.shape
+        z[:h * s, :w * s] = np.kron(y, np.ones((s, s)))
+        return O.blur_adjoint(z, O.gaussian_taps(sigma))
+    monkeypatch.setattr(O, "degrade_adjoint", adj_unscaled)
+    _fails(TD.test_degrade_adjoint_is_matrix_transpose, np.random.default_rng(0), 2)
+
+
+def test_dropped_regulariser_is_caught(monkeypatch):
+    orig = O.lle_weights
+    monkeypatch.setattr(O, "lle_weights", lambda q, nb, reg, d1: orig(q, nb, 0.0, d1))
+    _fails(TK.test_lle_k2_closed_form, np.random.default_rng(0))
+
+
+def test_descending_tie_rule_is_caught(monkeypatch):
+    def top_k_desc(qv, cand, feat, K):
+        d = ((feat[cand] - qv) ** 2).sum(axis=1)
+        order = np.lexsort((-cand, d))[:K]
+        return cand[order], d[order], 0
+    monkeypatch.setattr(O, "top_k", top_k_desc)
+    _fails(TK.test_top_k_is_sorted_brute_force_with_id_ties, np.random.default_rng(0))
+
+
+def test_off_by_one_hash_is_caught(monkeypatch):
+    orig = O.hash_values
+    monkeypatch.setattr(O, "hash_values", lambda v, a, b, w: (np.ceil(orig(v, a, b, w)[0] + 0.5).astype(np.int64), orig(v, a, b, w)[1]))
+    _fails(TH.test_unit_projection_reduces_to_floor, np.random.default_rng(0))
+
+
+def test_key_fold_without_position_salt_is_caught(monkeypatch):
+    def fold_no_salt(h, L, k):
+        n = h.shape[0]
+        keys = np.empty((n, L), np.uint64)
+        for l in range(L):
+            x = np.full(n, l, np.uint64)
+            for j in range(k):
+                x = O.mix64(x ^ ((h[:, l * k + j] & 0xFFFFFFFF).astype(np.uint64) + np.uint64(O.GOLDEN64)))
+            keys[:, l] = x
+        return keys
+    monkeypatch.setattr(O, "fold_keys", fold_no_salt)
+    _fails(TG.test_oracle_matches_golden_fixture)
+
+
+def test_overlap_sum_instead_of_mean_is_caught(monkeypatch):
+    def oa_sum(p, h, w, s, P):
+        PH = s * P
+        acc = np.zeros((s * h, s * w))
+        ii, jj = O.patch_origins(h, w, P)
+        for n in range(len(ii)):
+            acc[s * ii[n]:s * ii[n] + PH, s * jj[n]:s * jj[n] + PH] += p[n].reshape(PH, PH)
+        return acc
+    monkeypatch.setattr(O, "overlap_add", oa_sum)
+    _fails(TR.test_overlap_add_brute_force, np.random.default_rng(0))
+
+
+def test_missing_prior_factor_is_caught(monkeypatch):
+    orig = O.overlap_prior_grad
+    monkeypatch.setattr(O, "overlap_prior_grad", lambda p, h, w, s, P: 0.5 * orig(p, h, w, s, P))
+    _fails(TR.test_prior_gradient_matches_central_differences)
