@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Throughput of the patch-hashing zoom on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision 0|1] [--impl ours|reference] [--no-cpu-baseline]
+
+One step = one zoom_upscale of the workload's LR image (every hot-path stage:
+features, hashing, bin lookup, neighbour search, LLE, blend + overlap
+average, back-projection), inputs resident in HBM.  The default workload is
+the 2x zoom of a 512 x 512 LR image with a 1,000,000-pair dictionary
+(5x5 LR / 10x10 HR patches, L=16, k=16, K=8, 5 back-projection steps).
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank zooms its
+own copy of the workload on its own GPU (replicas, weak scaling); the
+reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth_inputs as S  # noqa: E402
+
+METRIC = "HR megapixels/s"
+UNIT = "MP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="zoom2x_512_dict1m")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-queries", type=int, default=24)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload_inputs(wl: S.Workload):
+    train = S.training_images(wl)
+    lrs = wl.train_hr // wl.scale
+    pos = S.sample_positions(wl.pos_seed, len(train), lrs, lrs, wl.patch, wl.n_pairs)
+    alpha, beta = S.lsh_draws(wl.proj_seed, wl.L, wl.k, wl.patch ** 2, wl.w)
+    lr = S.test_image(wl)
+    return train, pos, alpha, beta, lr
+
+
+def cpu_oracle_sample(wl: S.Workload, train, pos, alpha, beta, lr, n_sample: int):
+    """Times the oracle, as it stands, on a bounded sample of the workload and
+    extrapolates to HR megapixels/s: n_sample evenly spaced queries through
+    the per-patch steps (hash, candidates, top-K, LLE), the overlap average
+    of those patches, and back-projection on a 64-row HR band."""
+    from oracle import zoom_oracle as O
+    t0 = time.perf_counter()
+    od = O.build_dictionary(train, pos, wl.scale, wl.patch, wl.blur_sigma)
+    oi = O.build_index(od, alpha, beta, wl.w, wl.L, wl.k)
+    setup_s = time.perf_counter() - t0
+    P, s = wl.patch, wl.scale
+    nq = (wl.lr_h - P + 1) * (wl.lr_w - P + 1)
+    rows = np.linspace(0, nq - 1, n_sample).astype(np.int64)
+    t0 = time.perf_counter()
+    qr = O.query(lr, od, oi, wl.K, wl.reg_rel, rows=rows)
+    t_query = (time.perf_counter() - t0) / n_sample
+    t0 = time.perf_counter()
+    pt = O.blend_patches(qr.nbr, qr.wgt, qr.mu, od.hr_res)
+    t_blend = (time.perf_counter() - t0) / n_sample
+    band = min(64, s * wl.lr_h)
+    lrb = lr[:band // s].astype(np.float64)
+    xb = np.kron(lrb, np.ones((s, s)))
+    t0 = time.perf_counter()
+    O.back_project(xb, lrb, s, wl.blur_sigma, wl.bp_iters, wl.sigma_spatial, wl.sigma_range, wl.bp_radius)
+    t_bp_px = (time.perf_counter() - t0) / xb.size
+    hr_px = s * wl.lr_h * s * wl.lr_w
+    total = nq * (t_query + t_blend) + hr_px * t_bp_px
+    return {
+        "value": hr_px / 1e6 / total,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"{n_sample} of {nq} queries (hash, candidate union, FP64 top-{wl.K}, LLE, blend) "
+                   f"+ back-projection of a {band}-row HR band, extrapolated per query and per HR pixel"),
+        "seconds_per_query": t_query,
+        "mean_candidates_per_query": float(qr.n_cand.mean()),
+        "setup_s": setup_s,
+    }
+
+
+def gpu_launches_per_step(wl: S.Workload) -> int:
+    # features, hash, lookup, neighbour search, LLE, overlap-add, 2 per BP step
+    return 6 + 2 * wl.bp_iters
+
+
+def main():
+    a = parse()
+    wl = S.WORKLOADS[a.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    hr_px = wl.scale * wl.lr_h * wl.scale * wl.lr_w
+    nq = (wl.lr_h - wl.patch + 1) * (wl.lr_w - wl.patch + 1)
+    config = {"workload": wl.name, "lr": [wl.lr_h, wl.lr_w], "scale": wl.scale,
+              "dict_pairs": wl.n_pairs, "lr_patch": wl.patch, "L": wl.L, "k": wl.k, "K": wl.K,
+              "bp_iters": wl.bp_iters, "precision": "fp32-exact" if a.precision == 0 else "bf16-filter",
+              "parallelism": f"replicas{world}" if world > 1 else "single",
+              "l2": "inputs larger than L2 (dictionary features + HR patches stream from HBM each step)"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        train, pos, alpha, beta, lr = workload_inputs(wl)
+        vals = []
+        for i in range(a.warmup + a.steps):
+            r = cpu_oracle_sample(wl, train, pos, alpha, beta, lr, max(4, a.cpu_sample_queries // 4))
+            if i >= a.warmup:
+                vals.append(r["value"])
+        v = statistics.median(vals)
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": hr_px / 1e6 / v * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": config,
+               "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": r["sample"]},
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    import paper_1004_3980_gb300 as Z
+    from paper_1004_3980_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        B.build()
+    dev = local
+    torch.cuda.set_device(dev)
+    train, pos, alpha, beta, lr_np = workload_inputs(wl)
+
+    ctx = Z.Context(dev)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    imgs = [torch.from_numpy(x).cuda() for x in train]
+    e0.record(st)
+    d = Z.Dictionary(ctx, imgs, pos, wl.scale, wl.patch, wl.blur_sigma)
+    e1.record(st)
+    torch.cuda.synchronize()
+    dict_ms = e0.elapsed_time(e1)
+    e0.record(st)
+    ix = Z.Index(d, wl.L, wl.k, wl.w, alpha, beta)
+    e1.record(st)
+    torch.cuda.synchronize()
+    index_ms = e0.elapsed_time(e1)
+    del imgs
+
+    prm = Z.UpscaleParams(K=wl.K, reg_rel=wl.reg_rel, bp_iters=wl.bp_iters, sigma_spatial=wl.sigma_spatial,
+                          sigma_range=wl.sigma_range, bp_radius=wl.bp_radius, precision=a.precision)
+    lr = torch.from_numpy(lr_np).cuda()
+    out = torch.empty((wl.scale * wl.lr_h, wl.scale * wl.lr_w), device="cuda")
+    for _ in range(a.warmup):
+        Z.upscale(ix, lr, prm, out=out)
+    ctx.sync_status()
+    stats0 = ctx.stats()
+
+    # ---- timed region: K steps, device-resident inputs -------------------------
+    ctx.set_stage_timing(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stage_ms = {}
+    e0.record(st)
+    for _ in range(a.steps):
+        Z.upscale(ix, lr, prm, out=out)
+        sm = ctx.stats()["ms_stage"]       # reads this step's stage events
+        for k2, v in sm.items():
+            stage_ms[k2] = stage_ms.get(k2, 0.0) + v
+    e1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    ctx.set_stage_timing(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = world * hr_px / 1e6 / (ms_step / 1e3)
+    stats = ctx.stats()
+
+    # ---- end to end through the public API with host buffers -------------------
+    lr_host = torch.from_numpy(lr_np).pin_memory()
+    hr_host = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    lr_dev = torch.empty_like(lr)
+    for _ in range(2):
+        lr_dev.copy_(lr_host, non_blocking=True)
+        Z.upscale(ix, lr_dev, prm, out=out)
+        hr_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        lr_dev.copy_(lr_host, non_blocking=True)
+        Z.upscale(ix, lr_dev, prm, out=out)
+        hr_host.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = (time.perf_counter() - t0) / a.steps
+    e2e = {"value": world * hr_px / 1e6 / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": lr_host.numel() * 4, "d2h_bytes_per_step": hr_host.numel() * 4}
+
+    # ---- roofline of the dominant kernel -------------------------------------
+    knn_ms = stage_ms.get("knn", 0.0) / a.steps
+    d_feat = wl.patch ** 2
+    pairs = nq * wl.n_pairs
+    flops = pairs * 3.0 * d_feat            # per pair: d subtractions + d FMAs
+    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA peak at the maximum SM clock
+    achieved = flops / (knn_ms / 1e3) / 1e12 if knn_ms > 0 else None
+    roofline = {"kernel": "k_knn_exact (neighbour search, FP32 difference form)", "bound": "alu",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                "kernel_ms": knn_ms, "stage_share": knn_ms / ms_step if ms_step else None}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+           "lr_patch_queries_per_s": world * nq / (ms_step / 1e3),
+           "roofline": roofline, "e2e": e2e,
+           "gpu_launches": gpu_launches_per_step(wl) * a.steps, "clocks": clk,
+           "stage_ms_per_step": {k2: v / a.steps for k2, v in stage_ms.items()},
+           "mean_bucket_sum_per_query": stats["mean_bucket_sum"],
+           "dictionary_build_ms": dict_ms, "index_build_ms": index_ms,
+           "stats": {k2: v for k2, v in stats0.items() if k2 != "ms_stage"}}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_oracle_sample(wl, train, pos, alpha, beta, lr_np, a.cpu_sample_queries)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * zoom.h - C ABI of the GB300 (sm_103a) patch-hashing zoom library.
+ *
+ * Method: M. Das Gupta, "Hashing Image Patches for Zooming".  An LR image is
+ * zoomed by hashing every overlapping LR patch feature into L p-stable LSH
+ * tables (Sec. 4.1, Eq. 10), selecting the K nearest training patches among
+ * the hashed candidates (Sec. 4.2), solving the sum-to-one least-squares
+ * weights (Eq. 12-13), blending the paired HR patches (Eq. 14), averaging
+ * the overlaps, and refining with error back-projection through an
+ * approximate cross-bilateral filter (Sec. 4, Eq. 6-7; Sec. 4.3, Eq. 15-17).
+ *
+ * Conventions (every function):
+ *  - Returns a zoom_status; ZOOM_OK = 0.  Out-parameters are written only on
+ *    ZOOM_OK.  Nothing throws.  zoom_last_error() gives a one-line detail of
+ *    the last failure on the calling thread.
+ *  - "device" pointers are CUDA device memory of the context's device,
+ *    "host" pointers are CPU memory.  The caller owns every buffer it passes;
+ *    the library never frees or retains them past the call, except that an
+ *    asynchronous call reads and writes them on `stream` after returning.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls do not synchronise unless stated.
+ *  - Images are row-major float32, values on the [0, 1] scale.
+ *  - Handles own their device arrays, allocated through the context's
+ *    allocator.  An index refers to its dictionary: destroy the index first.
+ *  - A context is not thread-safe; use one per thread or serialise calls.
+ */
+#ifndef ZOOM_H
+#define ZOOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ZOOM_OK = 0,
+  ZOOM_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range   */
+  ZOOM_ERR_OOM = 2,         /* the allocator returned NULL                     */
+  ZOOM_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+  ZOOM_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up              */
+  ZOOM_ERR_UNSUPPORTED = 5, /* valid request outside what this build supports  */
+  ZOOM_ERR_STATE = 6,       /* handle used in the wrong state                  */
+  ZOOM_ERR_IO = 7,          /* file could not be read or written               */
+  ZOOM_ERR_DEVICE = 8       /* a kernel reported a failed check (status word)  */
+} zoom_status;
+
+typedef struct zoom_ctx_s* zoom_ctx;
+typedef struct zoom_dict_s* zoom_dict;
+typedef struct zoom_index_s* zoom_index;
+
+/* Device-memory allocator.  alloc returns device memory of at least `bytes`
+ * usable on `stream` (NULL on failure); free releases it (stream-ordered).
+ * A NULL allocator selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} zoom_allocator;
+
+/* Degradation and patch geometry (Sec. 2.1): HR -> Gaussian blur (3 taps,
+ * sigma blur_sigma, clamped borders) -> s x s box down-sampling.  LR patches
+ * are lr_patch x lr_patch; HR patches are (scale*lr_patch)^2.
+ * Supported: scale 1..4, lr_patch 2..7, blur_sigma > 0. */
+typedef struct {
+  int32_t scale;
+  int32_t lr_patch;
+  float blur_sigma;
+} zoom_degradation;
+
+/* LSH parameters (Sec. 3.2, Sec. 4.1).  L tables of k concatenated hashes
+ * h = floor((alpha.v + beta) / w).  min_table_hits = t (an ID is a candidate
+ * if it shares the query's bin in >= t tables; 1 = plain union).
+ * max_candidates: 0 = no cap; > 0 = the early stop of Sec. 4.2 (tables in
+ * order, IDs ascending within a bin, stop at exactly max_candidates).
+ * Supported: 1 <= L <= 32, 1 <= k <= 32, w > 0, 1 <= t <= L,
+ * 0 <= max_candidates <= 4096. */
+typedef struct {
+  int32_t L;
+  int32_t k;
+  float w;
+  int32_t min_table_hits;
+  int32_t max_candidates;
+} zoom_lsh_params;
+
+/* Inference parameters.  K nearest neighbours (1..16); reg_rel: the LLE
+ * regulariser eps = reg_rel * trace(G) (Eq. 12-13); bp_iters back-projection
+ * iterations (0..64) with spatial sigma sigma_spatial (pixels), range sigma
+ * sigma_range and window radius bp_radius (1..7) (Sec. 4.3).
+ * precision: 0 = exact FP32 neighbour search; 1 = BF16 tensor-core distance
+ * filter keeping the rerank_mult*K best, then FP32 exact rerank.
+ * fp64_cond_threshold: the LLE solve runs in FP64 for a query whose
+ * condition bound (trace(G) + eps) / eps exceeds it. */
+typedef struct {
+  int32_t K;
+  float reg_rel;
+  int32_t bp_iters;
+  float sigma_spatial;
+  float sigma_range;
+  int32_t bp_radius;
+  int32_t precision;
+  int32_t rerank_mult;
+  double fp64_cond_threshold;
+} zoom_upscale_params;
+
+/* Counters of the last zoom_query / zoom_upscale on a context (read after
+ * the stream has been synchronised; zoom_get_stats synchronises). */
+typedef struct {
+  int64_t n_queries;
+  double mean_bucket_sum;   /* mean over queries of sum_l |bin_l(q)| (with repeats) */
+  int64_t max_bucket_sum;
+  int64_t n_empty;          /* queries whose candidate set was empty          */
+  int64_t n_padded_queries; /* queries with fewer than K candidates (padded)  */
+  int64_t n_fp64_solves;    /* LLE solves that ran in FP64                    */
+  int64_t n_exact_match;    /* queries equal to a dictionary entry (one-hot)  */
+  int64_t n_filter_fallback;/* tensor-filter queries re-run on the exact path */
+  double ms_total;          /* device time of the last call (CUDA events)     */
+  /* per-stage device milliseconds of the last call, when stage timing is on:
+   * [0] features, [1] hashing, [2] bin lookup, [3] neighbour search,
+   * [4] LLE solve, [5] blend + overlap average, [6] back-projection */
+  double ms_stage[8];
+} zoom_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`; `alloc` may be NULL. */
+zoom_status zoom_ctx_create(int device, const zoom_allocator* alloc, zoom_ctx* out);
+void zoom_ctx_destroy(zoom_ctx ctx);
+const char* zoom_status_string(zoom_status s);
+/* Thread-local text of the last error (never NULL). */
+const char* zoom_last_error(void);
+
+/* ---- dictionary (Sec. 2.1; Sec. 5.1) ------------------------------------
+ * Builds N = n_pairs LR/HR training patch pairs.  hr_images: host array of
+ * n_images device pointers, image m of heights[m] x widths[m] (host arrays)
+ * float32 values.  Each image is degraded (blur + down-sampling; the LR
+ * image is rounded once to float32); pair n uses positions[n] = (image m,
+ * LR row i, LR col j) (host int32 [n_pairs][3]): LR patch at (i, j) and HR
+ * patch at (s*i, s*j).  Pair n gets ID n; positions should be sorted by
+ * (m, i, j) so that IDs follow the paper's row order.  Stored per pair:
+ * the LR pixels, the LR mean mu, the feature (pixels - mu) and the HR patch
+ * minus mu.  Errors: INVALID_ARG for sizes out of range or positions whose
+ * patch leaves its image (checked on the host). */
+zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
+                                  const int32_t* heights, const int32_t* widths,
+                                  int32_t n_images, const zoom_degradation* degr,
+                                  int64_t n_pairs, const int32_t* positions,
+                                  void* stream, zoom_dict* out);
+void zoom_dict_destroy(zoom_dict d);
+/* Copies stored arrays to the host (synchronises `stream`): lr_pix [N][P*P],
+ * mu [N], hr_res [N][(s*P)^2]; any pointer may be NULL. */
+zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_res, void* stream);
+/* Dictionary sizes: N, LR patch side P, scale s. */
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale);
+
+/* ---- LSH index (Sec. 3.2; Sec. 4.1, Eq. 10) -----------------------------
+ * Hashes every dictionary feature into L tables.  alpha: host float32
+ * [L*k][P*P] projection vectors; beta: host float32 [L*k] offsets in
+ * [0, w) (the random draws are inputs).  Builds, per table, the bucket key
+ * of every entry and a CSR of its bins (keys radix-sorted on the device).
+ * Errors: INVALID_ARG for parameters out of range. */
+zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const float* alpha,
+                             const float* beta, void* stream, zoom_index* out);
+void zoom_index_destroy(zoom_index ix);
+/* Copies the bucket key of every entry to host uint64 [N][L] and, if
+ * n_bins != NULL, the number of bins per table to host int32 [L]
+ * (synchronises `stream`). */
+zoom_status zoom_index_export(zoom_index ix, uint64_t* keys, int32_t* n_bins, void* stream);
+
+/* ---- inference ------------------------------------------------------------
+ * zoom_upscale: the whole per-patch inference and back-projection of an LR
+ * image lr (device, h x w) into hr (device, caller-allocated (s*h) x (s*w)).
+ * Requires h, w >= P.  scale must equal the dictionary's.  Device scratch
+ * memory comes from the context allocator.  Errors: INVALID_ARG (sizes,
+ * scale mismatch, K out of range), OOM, CUDA. */
+zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, int32_t scale,
+                         const zoom_upscale_params* prm, float* hr, void* stream);
+
+/* zoom_query: the per-patch steps only, for every LR patch origin (i, j) in
+ * row order, n_q = (h-P+1)(w-P+1).  Outputs (device, any may be NULL except
+ * nbr): keys uint64 [n_q][L] bucket keys of the query (Eq. 10 folded);
+ * nbr int32 [n_q][K] neighbour IDs in (distance, ID) order; dist float32
+ * [n_q][K] squared distances; wgt float32 [n_q][K] LLE weights (Eq. 12-13);
+ * mu float32 [n_q] patch means; bucket_sum int32 [n_q] sum of the L bin
+ * sizes. */
+zoom_status zoom_query(zoom_index ix, const float* lr, int32_t h, int32_t w,
+                       const zoom_upscale_params* prm, uint64_t* keys, int32_t* nbr, float* dist,
+                       float* wgt, float* mu, int32_t* bucket_sum, void* stream);
+
+/* zoom_reconstruct: Eq. 14 blend of the HR patches of given neighbours plus
+ * the overlap average (no back-projection).  nbr int32 [n_q][K], wgt float32
+ * [n_q][K], mu float32 [n_q] (device); hr device (s*h) x (s*w). */
+zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt, const float* mu,
+                             int32_t h, int32_t w, int32_t K, float* hr, void* stream);
+
+/* zoom_backproject: bp_iters iterations of the approximate cross-bilateral
+ * error back-projection (Sec. 4 Eq. 6-7, Sec. 4.3 Eq. 15-17) of the HR
+ * estimate hr (device, (s*h) x (s*w), updated in place) against the LR
+ * image lr (device, h x w), with the degradation `degr`. */
+zoom_status zoom_backproject(zoom_ctx ctx, const zoom_degradation* degr, const float* lr, int32_t h,
+                             int32_t w, const zoom_upscale_params* prm, float* hr, void* stream);
+
+/* zoom_get_stats: synchronises `stream` and returns the counters of the
+ * last zoom_query / zoom_upscale on ctx. */
+zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out);
+
+/* zoom_set_stage_timing: when enable != 0, zoom_query / zoom_upscale record
+ * CUDA events on their stream between stages (zoom_stats.ms_stage). */
+zoom_status zoom_set_stage_timing(zoom_ctx ctx, int32_t enable);
+
+/* zoom_sync_status: synchronises `stream` and reads (then clears) the
+ * context's device status word: ZOOM_OK, ZOOM_ERR_TIMEOUT or
+ * ZOOM_ERR_DEVICE. */
+zoom_status zoom_sync_status(zoom_ctx ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZOOM_H */

@@ -286,11 +286,11 @@ def candidate_set(index: LshIndex, qkeys: np.ndarray, min_hits: int = 1,
         return np.sort(np.array(order, np.int64))
     if not found:
         return np.empty(0, np.int64)
-    allids = np.concatenate(found)
-    if min_hits <= 1:
-        return np.unique(allids)
-    ids, cnt = np.unique(allids, return_counts=True)
-    return ids[cnt >= min_hits]
+    n = int(max((f.max() for f in found if len(f)), default=-1)) + 1
+    hits = np.zeros(max(n, 1), np.int32)
+    for ids in found:
+        hits[ids] += 1
+    return np.flatnonzero(hits >= max(min_hits, 1)).astype(np.int64)
 
 
 def top_k(qv: np.ndarray, cand: np.ndarray, feat: np.ndarray, K: int):

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) implementation of the per-patch inference of "Hashing Image
+Patches for Zooming" (Das Gupta): LSH hashing, exact nearest-neighbour
+selection among the hashed candidates, LLE weights, HR blend and overlap
+average, cross-bilateral error back-projection.
+
+The compute path is libzoom.so (hand-written CUDA behind the C ABI of
+include/zoom.h); this package only marshals arguments.
+"""
+from .zoom import (Context, Dictionary, Index, UpscaleParams, backproject, query,  # noqa: F401
+                   reconstruct, upscale)

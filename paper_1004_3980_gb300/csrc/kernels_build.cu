@@ -1,0 +1,418 @@
+// Dictionary and LSH index construction (Sec. 2.1, Sec. 3.2, Sec. 4.1).
+#include <math.h>
+
+#include <vector>
+
+#include "device_common.cuh"
+#include "zoom_internal.h"
+
+namespace {
+
+constexpr int kMaxScale = 4;
+
+// Combined blur+box weights of one output pixel, W_a * W_b over the
+// (s+2) x (s+2) window, as unevaluated float pairs hi + lo.
+struct PairWeights {
+  int n;  // s + 2
+  float hi[(kMaxScale + 2) * (kMaxScale + 2)];
+  float lo[(kMaxScale + 2) * (kMaxScale + 2)];
+};
+
+// 1-D weights of "3-tap Gaussian then s-box mean": output i reads input
+// s*i + a - 1, a in [0, s+2), with weight (1/s) * sum_{b + u = a} taps[u].
+void degrade_weights_1d(int s, float sigma, double* wts) {
+  double e = exp(-1.0 / (2.0 * (double)sigma * (double)sigma));
+  double t[3] = {e / (1.0 + 2.0 * e), 1.0 / (1.0 + 2.0 * e), e / (1.0 + 2.0 * e)};
+  for (int a = 0; a < s + 2; ++a) wts[a] = 0.0;
+  for (int b = 0; b < s; ++b)
+    for (int u = 0; u < 3; ++u) wts[b + u] += t[u] / s;
+}
+
+// LR[i][j] = sum_{a,b} W_a W_b HR[clamp(s i + a - 1)][clamp(s j + b - 1)],
+// accumulated as a float pair (two-sum / fma two-product) so that the final
+// float is the correctly rounded value of the exact sum in all but
+// vanishingly rare cases.  The dictionary stores this rounded LR image.
+__global__ void k_degrade_exact(const float* __restrict__ hr, int H, int W, int s, PairWeights pw,
+                                float* __restrict__ lr, int h, int w) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= h || j >= w) return;
+  float shi = 0.f, slo = 0.f;
+  for (int a = 0; a < pw.n; ++a) {
+    int r = zoom_clampi(s * i + a - 1, 0, H - 1);
+    for (int b = 0; b < pw.n; ++b) {
+      int c = zoom_clampi(s * j + b - 1, 0, W - 1);
+      float x = hr[(size_t)r * W + c];
+      float whi = pw.hi[a * pw.n + b], wlo = pw.lo[a * pw.n + b];
+      float p = x * whi;
+      float pe = fmaf(x, whi, -p);
+      pe = fmaf(x, wlo, pe);
+      float t = shi + p;
+      float bp = t - shi;
+      float err = (shi - (t - bp)) + (p - bp);
+      shi = t;
+      slo += err + pe;
+    }
+  }
+  lr[(size_t)i * w + j] = shi + slo;
+}
+
+template <int P>
+__global__ void k_dict_gather(const float* const* __restrict__ lr_images,
+                              const int32_t* __restrict__ lr_w,
+                              const float* const* __restrict__ hr_images,
+                              const int32_t* __restrict__ hr_w, const int32_t* __restrict__ pos,
+                              int64_t n, int s, int dpad, int ph2pad, float* __restrict__ lr_pix,
+                              float* __restrict__ feat, float* __restrict__ mu,
+                              float* __restrict__ norm2, float* __restrict__ hr_res) {
+  constexpr int D = P * P;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  int m = pos[e * 3 + 0], i = pos[e * 3 + 1], j = pos[e * 3 + 2];
+  const float* lr = lr_images[m];
+  int lw = lr_w[m];
+  float px[D], v[D], mean, n2;
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int b = 0; b < P; ++b) px[a * P + b] = lr[(size_t)(i + a) * lw + j + b];
+  zoom_patch_feature<D>(px, v, mean, n2);
+#pragma unroll
+  for (int q = 0; q < D; ++q) lr_pix[e * D + q] = px[q];
+  for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? v[q] : 0.f;
+  mu[e] = mean;
+  norm2[e] = n2;
+  const float* hr = hr_images[m];
+  int hw = hr_w[m];
+  int PH = s * P;
+  for (int a = 0; a < PH; ++a)
+    for (int b = 0; b < PH; ++b)
+      hr_res[e * ph2pad + a * PH + b] = hr[(size_t)(s * i + a) * hw + s * j + b] - mean;
+  for (int q = PH * PH; q < ph2pad; ++q) hr_res[e * ph2pad + q] = 0.f;
+}
+
+// Eq. 10 for every projection and the key fold of every table; one thread
+// per feature row.  alpha/beta are staged in shared memory.
+template <int D>
+__global__ void k_hash(const float* __restrict__ feat, int dpad, int64_t n,
+                       const float* __restrict__ alpha, const float* __restrict__ beta, int L, int k,
+                       float w, uint64_t* __restrict__ keys) {
+  extern __shared__ float s_ab[];
+  int nproj = L * k;
+  for (int t = threadIdx.x; t < nproj * D; t += blockDim.x) s_ab[t] = alpha[t];
+  for (int t = threadIdx.x; t < nproj; t += blockDim.x) s_ab[nproj * D + t] = beta[t];
+  __syncthreads();
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  float v[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) v[q] = feat[r * dpad + q];
+  const float* s_beta = s_ab + nproj * D;
+  for (int l = 0; l < L; ++l) {
+    uint64_t x = (uint64_t)l;
+    for (int j = 0; j < k; ++j) {
+      const float* a = s_ab + (l * k + j) * D;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc = fmaf(a[q], v[q], acc);
+      float t = acc + s_beta[l * k + j];
+      int h = (int)floorf(__fdiv_rn(t, w));
+      x = zoom_fold_step(x, h, j);
+    }
+    keys[r * L + l] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, int32 id) pairs, 8 bits per pass, stable.
+// ---------------------------------------------------------------------------
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_TILE = 4096;
+constexpr int SCAN_SEG = 4096;
+
+__global__ void k_extract_column(const uint64_t* __restrict__ src, int L, int l, int64_t n,
+                                 uint64_t* __restrict__ keys, int32_t* __restrict__ ids) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = src[i * L + l];
+  ids[i] = (int32_t)i;
+}
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             int32_t* __restrict__ hist, int ntiles) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int t = threadIdx.x; t < RS_TILE; t += RS_THREADS) {
+    int64_t g = base + t;
+    if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: items of a tile are ranked in index order.  The tile is
+// processed in chunks of 256 (one item per thread); within a chunk,
+// __match_any_sync groups lanes of equal digit, and per-digit prefix counts
+// over the warps give each item its place after all earlier items.
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                                int shift, const int32_t* __restrict__ offs, int ntiles) {
+  __shared__ int run[256];
+  __shared__ int wh[RS_THREADS / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < RS_TILE / RS_THREADS; ++c) {
+    int64_t g = (int64_t)blockIdx.x * RS_TILE + c * RS_THREADS + tid;
+    bool valid = g < n;
+    uint64_t key = valid ? kin[g] : 0ull;
+    int32_t val = valid ? vin[g] : 0;
+    int digit = valid ? (int)((key >> shift) & 255) : 256;
+    for (int q = tid; q < (RS_THREADS / 32) * 256; q += RS_THREADS) (&wh[0][0])[q] = 0;
+    __syncthreads();
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    int rank = __popc(peers & lt);
+    if (valid && rank == 0) wh[warp][digit] = __popc(peers);
+    __syncthreads();
+    {
+      int s = run[tid];
+#pragma unroll
+      for (int q = 0; q < RS_THREADS / 32; ++q) {
+        int t = wh[q][tid];
+        wh[q][tid] = s;
+        s += t;
+      }
+      run[tid] = s;
+    }
+    __syncthreads();
+    if (valid) {
+      int p = wh[warp][digit] + rank;
+      kout[p] = key;
+      vout[p] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of int32 in three phases: per-segment sums, a one-block
+// scan of the sums, per-segment scans with the segment offset.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  int excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0);
+  total = s_warp[nw - 1];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ part) {
+  __shared__ int s_warp[32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_SEG;
+  int acc = 0;
+  for (int t = threadIdx.x; t < SCAN_SEG; t += blockDim.x) {
+    int64_t g = base + t;
+    if (g < n) acc += in[g];
+  }
+  int total;
+  block_exclusive_scan(acc, s_warp, total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void k_scan_partials(int32_t* __restrict__ part, int np) {
+  __shared__ int s_warp[32];
+  // each thread scans a contiguous run of parts sequentially
+  const int per = (np + blockDim.x - 1) / blockDim.x;
+  int b0 = threadIdx.x * per;
+  int acc = 0;
+  for (int q = 0; q < per; ++q)
+    if (b0 + q < np) acc += part[b0 + q];
+  int total;
+  int ex = block_exclusive_scan(acc, s_warp, total);
+  for (int q = 0; q < per; ++q)
+    if (b0 + q < np) {
+      int t = part[b0 + q];
+      part[b0 + q] = ex;
+      ex += t;
+    }
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ part,
+                             int32_t* __restrict__ out) {
+  __shared__ int s_warp[32];
+  constexpr int PER = SCAN_SEG / 256;  // launched with 256 threads
+  int64_t base = (int64_t)blockIdx.x * SCAN_SEG + threadIdx.x * PER;
+  int v[PER];
+  int acc = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    int64_t g = base + q;
+    v[q] = g < n ? in[g] : 0;
+    acc += v[q];
+  }
+  int total;
+  int ex = block_exclusive_scan(acc, s_warp, total) + part[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    int64_t g = base + q;
+    if (g < n) out[g] = ex;
+    ex += v[q];
+  }
+}
+
+cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* part, cudaStream_t st) {
+  int nseg = (int)((n + SCAN_SEG - 1) / SCAN_SEG);
+  k_scan_reduce<<<nseg, 256, 0, st>>>(in, n, part);
+  k_scan_partials<<<1, 1024, 0, st>>>(part, nseg);
+  k_scan_apply<<<nseg, 256, 0, st>>>(in, n, part, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_csr_heads(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ head) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_csr_write(const uint64_t* __restrict__ keys, const int32_t* __restrict__ head,
+                            const int32_t* __restrict__ pos, int64_t n, uint64_t* __restrict__ ukeys,
+                            int32_t* __restrict__ offs, int32_t* __restrict__ nuniq) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (head[i]) {
+    ukeys[pos[i]] = keys[i];
+    offs[pos[i]] = (int32_t)i;
+  }
+  if (i == n - 1) {
+    int32_t u = pos[i] + head[i];
+    offs[u] = (int32_t)n;
+    *nuniq = u;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, float sigma, float* lr,
+                                 cudaStream_t st) {
+  double w1[kMaxScale + 2];
+  degrade_weights_1d(s, sigma, w1);
+  PairWeights pw;
+  pw.n = s + 2;
+  for (int a = 0; a < s + 2; ++a)
+    for (int b = 0; b < s + 2; ++b) {
+      double p = w1[a] * w1[b];
+      float hi = (float)p;
+      pw.hi[a * pw.n + b] = hi;
+      pw.lo[a * pw.n + b] = (float)(p - (double)hi);
+    }
+  int h = H / s, w = W / s;
+  dim3 blk(32, 8), grd((w + 31) / 32, (h + 7) / 8);
+  k_degrade_exact<<<grd, blk, 0, st>>>(hr, H, W, s, pw, lr, h, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_w,
+                               const float* const* d_hr_images, const int32_t* d_hr_w,
+                               const int32_t* d_pos, int64_t n, int P, int s, zoom_dict d,
+                               cudaStream_t st) {
+  int blocks = (int)((n + 127) / 128);
+  if (P == 3)
+    k_dict_gather<3><<<blocks, 128, 0, st>>>(d_lr_images, d_lr_w, d_hr_images, d_hr_w, d_pos, n, s,
+                                             d->dpad, d->ph2pad, d->lr_pix, d->feat, d->mu,
+                                             d->norm2, d->hr_res);
+  else if (P == 5)
+    k_dict_gather<5><<<blocks, 128, 0, st>>>(d_lr_images, d_lr_w, d_hr_images, d_hr_w, d_pos, n, s,
+                                             d->dpad, d->ph2pad, d->lr_pix, d->feat, d->mu,
+                                             d->norm2, d->hr_res);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const float* alpha,
+                        const float* beta, int L, int k, float w, uint64_t* keys, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  size_t smem = (size_t)L * k * (d + 1) * sizeof(float);
+  int blocks = (int)((n + 127) / 128);
+  if (d == 9) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_hash<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hash<9><<<blocks, 128, smem, st>>>(feat, dpad, n, alpha, beta, L, k, w, keys);
+  } else if (d == 25) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_hash<25>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hash<25><<<blocks, 128, smem, st>>>(feat, dpad, n, alpha, beta, L, k, w, keys);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+size_t csr_scratch_bytes(int64_t n) {
+  int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  int64_t hist = 256 * ntiles;
+  int64_t nseg = (std::max<int64_t>(hist, n) + SCAN_SEG - 1) / SCAN_SEG;
+  // keys x2, ids x2, hist, head, pos, parts
+  return (size_t)(2 * n * 8 + 2 * n * 4 + hist * 4 + 2 * n * 4 + nseg * 4 + 1024);
+}
+
+cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  const int64_t n = ix->dict->n;
+  const int L = ix->L;
+  if (scratch_bytes < csr_scratch_bytes(n)) return cudaErrorInvalidValue;
+  const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+  char* p = (char*)scratch;
+  uint64_t* ka = (uint64_t*)p; p += n * 8;
+  uint64_t* kb = (uint64_t*)p; p += n * 8;
+  int32_t* va = (int32_t*)p; p += n * 4;
+  int32_t* vb = (int32_t*)p; p += n * 4;
+  int32_t* hist = (int32_t*)p; p += (int64_t)256 * ntiles * 4;
+  int32_t* head = (int32_t*)p; p += n * 4;
+  int32_t* pos = (int32_t*)p; p += n * 4;
+  int32_t* part = (int32_t*)p;
+  const int eb = (int)((n + 255) / 256);
+  for (int l = 0; l < L; ++l) {
+    k_extract_column<<<eb, 256, 0, st>>>(ix->dkeys, L, l, n, ka, va);
+    uint64_t* kin = ka; uint64_t* kout = kb;
+    int32_t* vin = va; int32_t* vout = vb;
+    for (int shift = 0; shift < 64; shift += 8) {
+      k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+      cudaError_t e = exclusive_scan(hist, hist, (int64_t)256 * ntiles, part, st);
+      if (e != cudaSuccess) return e;
+      k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
+      std::swap(kin, kout);
+      std::swap(vin, vout);
+    }
+    // after 8 passes the sorted data is back in ka / va
+    k_csr_heads<<<eb, 256, 0, st>>>(kin, n, head);
+    cudaError_t e = exclusive_scan(head, pos, n, part, st);
+    if (e != cudaSuccess) return e;
+    k_csr_write<<<eb, 256, 0, st>>>(kin, head, pos, n, ix->ukeys + (int64_t)l * n,
+                                    ix->offs + (int64_t)l * (n + 1), ix->nuniq + l);
+    cudaMemcpyAsync(ix->ids + (int64_t)l * n, vin, n * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,141 @@
+// HR image steps: blend + overlap average (Eq. 14; averaging of overlaps)
+// and the error back-projection with the approximate cross-bilateral filter
+// (Sec. 4, Eq. 6-7; Sec. 4.3, Eq. 15-17).
+#include <math.h>
+
+#include "device_common.cuh"
+#include "zoom_internal.h"
+
+namespace {
+
+// Gather form: each HR pixel sums, over the patches covering it, the
+// patch's blended value mu_n + sum_m w_nm R[nbr_nm] at its offset, and
+// divides by the number of covering patches.  No atomics.
+__global__ void k_overlap_add(const int32_t* __restrict__ nbr, const float* __restrict__ wgt,
+                              const float* __restrict__ mu, const float* __restrict__ hr_res,
+                              int ph2pad, int K, int h, int w, int s, int P,
+                              float* __restrict__ hr) {
+  const int W = s * w, H = s * h;
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= W || Y >= H) return;
+  const int PH = s * P, nh = h - P + 1, nw = w - P + 1;
+  const int i_hi = min(Y / s, nh - 1), j_hi = min(X / s, nw - 1);
+  const int i_lo = Y >= PH ? (Y - PH) / s + 1 : 0;
+  const int j_lo = X >= PH ? (X - PH) / s + 1 : 0;
+  float acc = 0.f;
+  int cnt = 0;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    for (int j = j_lo; j <= j_hi; ++j) {
+      const int64_t n = (int64_t)i * nw + j;
+      const int off = (Y - s * i) * PH + (X - s * j);
+      float v = mu[n];
+      for (int m = 0; m < K; ++m)
+        v = fmaf(wgt[n * K + m], hr_res[(int64_t)nbr[n * K + m] * ph2pad + off], v);
+      acc += v;
+      ++cnt;
+    }
+  }
+  hr[(int64_t)Y * W + X] = acc / (float)cnt;
+}
+
+// e = D(B x) - y on the LR grid (FP32).  The blur and the box mean combine
+// into separable 1-D weights over the (s+2)-wide window.
+struct Wts1D {
+  int n;
+  float w[8];
+};
+
+__global__ void k_bp_error(const float* __restrict__ x, int H, int W, const float* __restrict__ y,
+                           int h, int w, int s, Wts1D wt, float* __restrict__ e) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= h || j >= w) return;
+  float acc = 0.f;
+  for (int a = 0; a < wt.n; ++a) {
+    const int r = zoom_clampi(s * i + a - 1, 0, H - 1);
+    float row = 0.f;
+    for (int b = 0; b < wt.n; ++b) {
+      const int c = zoom_clampi(s * j + b - 1, 0, W - 1);
+      row = fmaf(wt.w[b], x[(int64_t)r * W + c], row);
+    }
+    acc = fmaf(wt.w[a], row, acc);
+  }
+  e[(int64_t)i * w + j] = acc - y[(int64_t)i * w + j];
+}
+
+// x' = x - r * G, G = normalised spatial Gaussian over the replicated LR
+// error, r = exp(-(x - mean_Gamma x)^2 / (2 sigma_r^2)); clamped borders.
+struct Gauss1D {
+  int R;
+  float c[16];
+};
+
+__global__ void k_bp_update(const float* __restrict__ x, float* __restrict__ xo, int H, int W,
+                            const float* __restrict__ e, int w, int s, Gauss1D g,
+                            float inv_two_sr2) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= W || Y >= H) return;
+  const int R = g.R;
+  float gs = 0.f, box = 0.f;
+  for (int dy = -R; dy <= R; ++dy) {
+    const int yy = zoom_clampi(Y + dy, 0, H - 1);
+    float grow = 0.f, brow = 0.f;
+    for (int dx = -R; dx <= R; ++dx) {
+      const int xx = zoom_clampi(X + dx, 0, W - 1);
+      grow = fmaf(g.c[dx + R], e[(int64_t)(yy / s) * w + xx / s], grow);
+      brow += x[(int64_t)yy * W + xx];
+    }
+    gs = fmaf(g.c[dy + R], grow, gs);
+    box += brow;
+  }
+  const float m = box / (float)((2 * R + 1) * (2 * R + 1));
+  const float xv = x[(int64_t)Y * W + X];
+  const float dv = xv - m;
+  const float r = expf(-dv * dv * inv_two_sr2);
+  xo[(int64_t)Y * W + X] = xv - r * gs;
+}
+
+}  // namespace
+
+cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float* mu,
+                               const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
+                               float* hr, cudaStream_t st) {
+  dim3 blk(32, 8), grd((s * w + 31) / 32, (s * h + 7) / 8);
+  k_overlap_add<<<grd, blk, 0, st>>>(nbr, wgt, mu, hr_res, ph2pad, K, h, w, s, P, hr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, float* err, int h,
+                                int w, int s, float blur_sigma, float sigma_sp, float sigma_r,
+                                int radius, cudaStream_t st) {
+  const int H = s * h, W = s * w;
+  Wts1D wt;
+  {
+    double e = exp(-1.0 / (2.0 * (double)blur_sigma * (double)blur_sigma));
+    double t[3] = {e / (1.0 + 2.0 * e), 1.0 / (1.0 + 2.0 * e), e / (1.0 + 2.0 * e)};
+    double acc[8] = {0};
+    for (int b = 0; b < s; ++b)
+      for (int u = 0; u < 3; ++u) acc[b + u] += t[u] / s;
+    wt.n = s + 2;
+    for (int a = 0; a < 8; ++a) wt.w[a] = (float)acc[a];
+  }
+  Gauss1D g;
+  {
+    g.R = radius;
+    double c[16], tot = 0.0;
+    for (int d = -radius; d <= radius; ++d) {
+      c[d + radius] = exp(-(double)(d * d) / (2.0 * (double)sigma_sp * (double)sigma_sp));
+      tot += c[d + radius];
+    }
+    for (int d = 0; d < 16; ++d) g.c[d] = d < 2 * radius + 1 ? (float)(c[d] / tot) : 0.f;
+  }
+  dim3 blk(32, 8);
+  dim3 g1((w + 31) / 32, (h + 7) / 8);
+  k_bp_error<<<g1, blk, 0, st>>>(x, H, W, lr, h, w, s, wt, err);
+  dim3 g2((W + 31) / 32, (H + 7) / 8);
+  const float inv = (float)(1.0 / (2.0 * (double)sigma_r * (double)sigma_r));
+  k_bp_update<<<g2, blk, 0, st>>>(x, x_out, H, W, err, w, s, g, inv);
+  return cudaGetLastError();
+}

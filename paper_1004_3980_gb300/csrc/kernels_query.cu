@@ -1,0 +1,400 @@
+// Per-patch inference steps (Sec. 4.1-4.2): query features, bin lookup,
+// exact K-nearest selection over the hashed candidate set, LLE weights.
+#include <float.h>
+#include <limits.h>
+
+#include "device_common.cuh"
+#include "zoom_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// query features: every P x P patch of the LR image at stride 1, row order
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void k_query_features(const float* __restrict__ lr, int h, int w, int dpad,
+                                 float* __restrict__ feat, float* __restrict__ mu,
+                                 float* __restrict__ norm2) {
+  constexpr int D = P * P;
+  const int nw = w - P + 1;
+  const int64_t nq = (int64_t)(h - P + 1) * nw;
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  int i = (int)(q / nw), j = (int)(q % nw);
+  float px[D], v[D], m, n2;
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int b = 0; b < P; ++b) px[a * P + b] = lr[(size_t)(i + a) * w + j + b];
+  zoom_patch_feature<D>(px, v, m, n2);
+  for (int t = 0; t < dpad; ++t) feat[q * dpad + t] = t < D ? v[t] : 0.f;
+  mu[q] = m;
+  if (norm2) norm2[q] = n2;
+}
+
+// ---------------------------------------------------------------------------
+// bin lookup: binary search of each table's query key among its bin keys
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_lookup(const uint64_t* __restrict__ qkeys, int64_t nq, int L,
+                                const uint64_t* __restrict__ ukeys, const int32_t* __restrict__ offs,
+                                const int32_t* __restrict__ nuniq, int64_t N,
+                                int32_t* __restrict__ bucket_sum,
+                                unsigned long long* __restrict__ counters) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  long long tot = 0;
+  for (int l = 0; l < L; ++l) {
+    const uint64_t key = qkeys[q * L + l];
+    const uint64_t* uk = ukeys + (int64_t)l * N;
+    int lo = 0, hi = nuniq[l];
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (uk[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo < nuniq[l] && uk[lo] == key) {
+      const int32_t* of = offs + (int64_t)l * (N + 1);
+      tot += of[lo + 1] - of[lo];
+    }
+  }
+  if (bucket_sum) bucket_sum[q] = (int32_t)tot;
+  atomicAdd(&counters[CNT_BUCKET_SUM], (unsigned long long)tot);
+  atomicMax(&counters[CNT_BUCKET_MAX], (unsigned long long)tot);
+}
+
+// ---------------------------------------------------------------------------
+// Exact K nearest in the candidate set (Sec. 4.2), SIMT FP32.
+//
+// The candidate set C(q) (entries sharing the query's bin in >= t of the L
+// tables) is nearly the whole dictionary at the workloads' bin widths, so
+// the dictionary is streamed densely through shared memory and membership
+// is tested only for entries that would enter the list.  Order key:
+// (not a member, squared distance in FP32 difference form, ID); members thus
+// precede every non-member, which pads queries with fewer than K candidates
+// by their nearest non-members.  Entries arrive in ascending ID, so a tie in
+// distance never displaces an earlier entry.
+// ---------------------------------------------------------------------------
+struct Cand {
+  float d;
+  int id;
+  int flag;  // 0 member, 1 non-member, 2 empty slot
+};
+
+__device__ __forceinline__ bool cand_less(const Cand& a, const Cand& b) {
+  if (a.flag != b.flag) return a.flag < b.flag;
+  if (a.d != b.d) return a.d < b.d;
+  return a.id < b.id;
+}
+
+template <int KMAX>
+__device__ __forceinline__ void list_insert(Cand (&bl)[KMAX], int K, const Cand& c) {
+  bool done = false;
+#pragma unroll
+  for (int j = KMAX - 1; j > 0; --j) {
+    if (j < K && !done) {
+      if (cand_less(c, bl[j - 1])) {
+        bl[j] = bl[j - 1];
+      } else {
+        bl[j] = c;
+        done = true;
+      }
+    }
+  }
+  if (!done) bl[0] = c;
+}
+
+template <int KMAX>
+__device__ __forceinline__ Cand list_worst(const Cand (&bl)[KMAX], int K) {
+  Cand w = bl[0];
+#pragma unroll
+  for (int j = 1; j < KMAX; ++j)
+    if (j == K - 1) w = bl[j];
+  return w;
+}
+
+constexpr int KNN_THREADS = 128;
+constexpr int KNN_TN = 64;
+
+template <int D, int KMAX>
+__global__ __launch_bounds__(KNN_THREADS) void k_knn_exact(
+    const float* __restrict__ qfeat, int dpad, int64_t nq, const uint64_t* __restrict__ qkeys,
+    const float* __restrict__ dfeat, int64_t N, const uint64_t* __restrict__ dkeys, int L, int tmin,
+    int K, int32_t* __restrict__ nbr, float* __restrict__ dist,
+    unsigned long long* __restrict__ counters) {
+  constexpr int DP = (D + 3) / 4 * 4;
+  __shared__ __align__(16) float tile[KNN_TN * DP];
+  const int64_t q = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
+  const bool active = q < nq;
+  float qv[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) qv[i] = active ? qfeat[q * dpad + i] : 0.f;
+  Cand bl[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) bl[j] = Cand{FLT_MAX, INT_MAX, 2};
+  float thr = FLT_MAX;  // fast-path bound: only d < thr can enter the list
+  bool thr_inf = true;
+
+  for (int64_t base = 0; base < N; base += KNN_TN) {
+    const int nt = (int)((N - base) < KNN_TN ? (N - base) : KNN_TN);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt * (DP / 4); t += KNN_THREADS) {
+      int r = t / (DP / 4), c4 = t % (DP / 4);
+      reinterpret_cast<float4*>(tile)[t] =
+          reinterpret_cast<const float4*>(dfeat + (base + r) * dpad)[c4];
+    }
+    __syncthreads();
+    if (!active) continue;
+    for (int c = 0; c < nt; ++c) {
+      const float* cv = tile + c * DP;
+      float dd = 0.f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        float df = qv[i] - cv[i];
+        dd = fmaf(df, df, dd);
+      }
+      if (thr_inf || dd < thr) {
+        const int64_t id = base + c;
+        int hits = 0;
+        for (int l = 0; l < L; ++l) hits += (qkeys[q * L + l] == dkeys[id * L + l]) ? 1 : 0;
+        Cand cd{dd, (int)id, hits >= tmin ? 0 : 1};
+        Cand wst = list_worst<KMAX>(bl, K);
+        if (cand_less(cd, wst)) {
+          list_insert<KMAX>(bl, K, cd);
+          wst = list_worst<KMAX>(bl, K);
+          thr_inf = wst.flag != 0;
+          thr = wst.d;
+        }
+      }
+    }
+  }
+  if (!active) return;
+  int npad = 0;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < K) {
+      nbr[q * K + j] = bl[j].id;
+      dist[q * K + j] = bl[j].d;
+      npad += bl[j].flag != 0 ? 1 : 0;
+    }
+  }
+  if (npad > 0) atomicAdd(&counters[CNT_PADDED], 1ull);
+  if (npad == K) atomicAdd(&counters[CNT_EMPTY], 1ull);
+}
+
+// ---------------------------------------------------------------------------
+// LLE weights (Eq. 12-13): G = Z Z^T over the K neighbours, C = G + eps I,
+// eps = reg_rel * trace(G), Cholesky, C z = 1, w = z / sum(z).  One thread
+// per query.  FP64 when the condition bound (trace + eps) / eps exceeds the
+// threshold or an FP32 pivot is not positive.  A query at distance exactly 0
+// from its first neighbour gets the one-hot weight.
+// ---------------------------------------------------------------------------
+template <typename T, int KMAX>
+__device__ __forceinline__ bool chol_solve(T (&C)[KMAX][KMAX], int K, T (&z)[KMAX]) {
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < K) {
+      T s = C[j][j];
+#pragma unroll
+      for (int m = 0; m < j; ++m) s -= C[j][m] * C[j][m];
+      if (!(s > T(0))) return false;
+      T ljj = sqrt(s);
+      C[j][j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < KMAX; ++i) {
+        if (i < K) {
+          T t = C[i][j];
+#pragma unroll
+          for (int m = 0; m < j; ++m) t -= C[i][m] * C[j][m];
+          C[i][j] = t / ljj;
+        }
+      }
+    }
+  }
+  T u[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) {
+    if (i < K) {
+      T t = T(1);
+#pragma unroll
+      for (int m = 0; m < i; ++m) t -= C[i][m] * u[m];
+      u[i] = t / C[i][i];
+    }
+  }
+#pragma unroll
+  for (int i = KMAX - 1; i >= 0; --i) {
+    if (i < K) {
+      T t = u[i];
+#pragma unroll
+      for (int m = i + 1; m < KMAX; ++m)
+        if (m < K) t -= C[m][i] * z[m];
+      z[i] = t / C[i][i];
+    }
+  }
+  return true;
+}
+
+template <int D, int KMAX>
+__global__ __launch_bounds__(128) void k_lle(const float* __restrict__ qfeat, int dpad, int64_t nq,
+                                             const float* __restrict__ dfeat,
+                                             const int32_t* __restrict__ nbr,
+                                             const float* __restrict__ dist, int K, float reg_rel,
+                                             double cond_thr, float* __restrict__ wgt,
+                                             unsigned long long* __restrict__ counters) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  if (dist[q * K] == 0.f) {
+    for (int j = 0; j < K; ++j) wgt[q * K + j] = j == 0 ? 1.f : 0.f;
+    atomicAdd(&counters[CNT_EXACT], 1ull);
+    return;
+  }
+  int id[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) id[j] = j < K ? nbr[q * K + j] : 0;
+  float G[KMAX][KMAX];
+#pragma unroll
+  for (int a = 0; a < KMAX; ++a)
+#pragma unroll
+    for (int b = 0; b < KMAX; ++b) G[a][b] = 0.f;
+  for (int i = 0; i < D; ++i) {
+    float qi = qfeat[q * dpad + i];
+    float z[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) z[j] = j < K ? qi - dfeat[(int64_t)id[j] * dpad + i] : 0.f;
+#pragma unroll
+    for (int a = 0; a < KMAX; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) G[a][b] = fmaf(z[a], z[b], G[a][b]);
+  }
+  float tr = 0.f;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j)
+    if (j < K) tr += G[j][j];
+  const float eps = reg_rel * tr;
+  const double cond = ((double)tr + (double)eps) / (double)eps;
+  float w[KMAX];
+  bool ok = false;
+  if (cond <= cond_thr) {
+    float C[KMAX][KMAX];
+#pragma unroll
+    for (int a = 0; a < KMAX; ++a)
+#pragma unroll
+      for (int b = 0; b < KMAX; ++b) C[a][b] = (b <= a ? G[a][b] : G[b][a]) + (a == b ? eps : 0.f);
+    float z[KMAX];
+    ok = chol_solve<float, KMAX>(C, K, z);
+    if (ok) {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j < K) s += z[j];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j) w[j] = z[j] / s;
+    }
+  }
+  if (!ok) {
+    // FP64 Gram and Cholesky from the FP32 features
+    double Gd[KMAX][KMAX];
+#pragma unroll
+    for (int a = 0; a < KMAX; ++a)
+#pragma unroll
+      for (int b = 0; b < KMAX; ++b) Gd[a][b] = 0.0;
+    for (int i = 0; i < D; ++i) {
+      double qi = qfeat[q * dpad + i];
+      double z[KMAX];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j) z[j] = j < K ? qi - (double)dfeat[(int64_t)id[j] * dpad + i] : 0.0;
+#pragma unroll
+      for (int a = 0; a < KMAX; ++a)
+#pragma unroll
+        for (int b = 0; b < KMAX; ++b) Gd[a][b] += z[a] * z[b];
+    }
+    double trd = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < K) trd += Gd[j][j];
+    const double epsd = (double)reg_rel * trd;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) Gd[j][j] += epsd;
+    double zd[KMAX];
+    bool okd = chol_solve<double, KMAX>(Gd, K, zd);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < K) s += okd ? zd[j] : 1.0;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) w[j] = (float)((okd ? zd[j] : 1.0) / s);
+    atomicAdd(&counters[CNT_FP64], 1ull);
+  }
+  for (int j = 0; j < K; ++j) wgt[q * K + j] = w[j];
+}
+
+template <int D>
+cudaError_t knn_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
+                           int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                           cudaStream_t st) {
+  zoom_dict d = ix->dict;
+  int blocks = (int)((nq + KNN_THREADS - 1) / KNN_THREADS);
+  if (K <= 8)
+    k_knn_exact<D, 8><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
+                                                     ix->dkeys, ix->L, ix->t, K, nbr, dist,
+                                                     counters);
+  else
+    k_knn_exact<D, 16><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
+                                                      ix->dkeys, ix->L, ix->t, K, nbr, dist,
+                                                      counters);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t lle_dispatch_k(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
+                           const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
+                           unsigned long long* counters, cudaStream_t st) {
+  int blocks = (int)((nq + 127) / 128);
+  if (K <= 8)
+    k_lle<D, 8><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, d->feat, nbr, dist, K, reg_rel,
+                                        cond_thr, wgt, counters);
+  else
+    k_lle<D, 16><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, d->feat, nbr, dist, K, reg_rel,
+                                         cond_thr, wgt, counters);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_query_features(const float* lr, int h, int w, int P, int dpad, float* feat,
+                                  float* mu, float* norm2, cudaStream_t st) {
+  int64_t nq = (int64_t)(h - P + 1) * (w - P + 1);
+  int blocks = (int)((nq + 127) / 128);
+  if (P == 3)
+    k_query_features<3><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
+  else if (P == 5)
+    k_query_features<5><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t nq,
+                                 int32_t* bucket_sum, unsigned long long* counters,
+                                 cudaStream_t st) {
+  int blocks = (int)((nq + 127) / 128);
+  k_bucket_lookup<<<blocks, 128, 0, st>>>(qkeys, nq, ix->L, ix->ukeys, ix->offs, ix->nuniq,
+                                          ix->dict->n, bucket_sum, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
+                             int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                             cudaStream_t st) {
+  if (ix->dict->d == 9) return knn_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, st);
+  if (ix->dict->d == 25) return knn_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
+                       const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
+                       unsigned long long* counters, cudaStream_t st) {
+  if (d->d == 9)
+    return lle_dispatch_k<9>(d, qfeat, nq, nbr, dist, K, reg_rel, cond_thr, wgt, counters, st);
+  if (d->d == 25)
+    return lle_dispatch_k<25>(d, qfeat, nq, nbr, dist, K, reg_rel, cond_thr, wgt, counters, st);
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,671 @@
+// C ABI of the zoom library: argument checks, handles, orchestration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "zoom_internal.h"
+
+namespace {
+thread_local std::string g_last_error = "";
+
+zoom_status fail(zoom_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define ZCHECK_CUDA(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ZOOM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Scratch {
+  zoom_ctx ctx;
+  cudaStream_t st;
+  void* p = nullptr;
+  size_t bytes = 0;
+  Scratch(zoom_ctx c, cudaStream_t s) : ctx(c), st(s) {}
+  bool get(size_t b) {
+    bytes = b;
+    p = zoom_alloc(ctx, b, st);
+    return p != nullptr || b == 0;
+  }
+  ~Scratch() {
+    if (p) zoom_free(ctx, p, bytes, st);
+  }
+};
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* r = (T*)(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return r;
+  }
+};
+
+bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string& why) {
+  if (!p) { why = "params is NULL"; return false; }
+  if (p->K < 1 || p->K > 16) { why = "K must be in 1..16"; return false; }
+  if (p->K > d->n) { why = "K exceeds the dictionary size"; return false; }
+  if (!(p->reg_rel >= 0.f) || !isfinite(p->reg_rel)) { why = "reg_rel must be >= 0"; return false; }
+  if (p->bp_iters < 0 || p->bp_iters > 64) { why = "bp_iters must be in 0..64"; return false; }
+  if (p->bp_iters > 0) {
+    if (p->bp_radius < 1 || p->bp_radius > 7) { why = "bp_radius must be in 1..7"; return false; }
+    if (!(p->sigma_spatial > 0.f) || !(p->sigma_range > 0.f)) { why = "sigmas must be > 0"; return false; }
+  }
+  if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return false; }
+  if (p->precision == 1 && (p->rerank_mult < 1 || p->rerank_mult * p->K > 64)) {
+    why = "rerank_mult * K must be in K..64"; return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+void zoom_set_error(const std::string& msg) { g_last_error = msg; }
+
+void zoom_stage_mark(zoom_ctx ctx, int i, cudaStream_t st) {
+  if (!ctx->stage_timing || i < 0 || i > 8) return;
+  if (cudaEventRecord(ctx->stage_ev[i], st) == cudaSuccess) ctx->stage_rec[i] = true;
+}
+
+void* zoom_alloc(zoom_ctx ctx, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return nullptr;
+  if (ctx->has_alloc) return ctx->alloc.alloc(bytes, (void*)st, ctx->alloc.user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  if (ctx->has_alloc) {
+    ctx->alloc.free(p, bytes, (void*)st, ctx->alloc.user);
+    return;
+  }
+  cudaFreeAsync(p, st);
+}
+
+extern "C" {
+
+const char* zoom_status_string(zoom_status s) {
+  switch (s) {
+    case ZOOM_OK: return "ok";
+    case ZOOM_ERR_INVALID_ARG: return "invalid argument";
+    case ZOOM_ERR_OOM: return "out of device memory";
+    case ZOOM_ERR_CUDA: return "CUDA error";
+    case ZOOM_ERR_TIMEOUT: return "device wait timed out";
+    case ZOOM_ERR_UNSUPPORTED: return "unsupported";
+    case ZOOM_ERR_STATE: return "invalid handle state";
+    case ZOOM_ERR_IO: return "I/O error";
+    case ZOOM_ERR_DEVICE: return "device-side check failed";
+  }
+  return "unknown status";
+}
+
+const char* zoom_last_error(void) { return g_last_error.c_str(); }
+
+zoom_status zoom_ctx_create(int device, const zoom_allocator* alloc, zoom_ctx* out) {
+  if (!out) return fail(ZOOM_ERR_INVALID_ARG, "out is NULL");
+  int n = 0;
+  ZCHECK_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(ZOOM_ERR_INVALID_ARG, "no such device");
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(ZOOM_ERR_INVALID_ARG, "allocator needs both alloc and free");
+  ZCHECK_CUDA(cudaSetDevice(device));
+  zoom_ctx c = new zoom_ctx_s();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (alloc) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  if (cudaMalloc(&c->d_status, 64) != cudaSuccess ||
+      cudaMalloc(&c->d_counters, CNT_N * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(c->d_status);
+    delete c;
+    return fail(ZOOM_ERR_OOM, "context buffers");
+  }
+  cudaMemset(c->d_status, 0, 64);
+  cudaMemset(c->d_counters, 0, CNT_N * sizeof(unsigned long long));
+  cudaEventCreate(&c->ev0);
+  cudaEventCreate(&c->ev1);
+  for (int i = 0; i < 9; ++i) cudaEventCreate(&c->stage_ev[i]);
+  *out = c;
+  return ZOOM_OK;
+}
+
+void zoom_ctx_destroy(zoom_ctx c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->d_status);
+  cudaFree(c->d_counters);
+  cudaEventDestroy(c->ev0);
+  cudaEventDestroy(c->ev1);
+  for (int i = 0; i < 9; ++i) cudaEventDestroy(c->stage_ev[i]);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// dictionary
+// ---------------------------------------------------------------------------
+
+zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
+                                  const int32_t* heights, const int32_t* widths,
+                                  int32_t n_images, const zoom_degradation* degr,
+                                  int64_t n_pairs, const int32_t* positions, void* stream,
+                                  zoom_dict* out) {
+  if (!ctx || !hr_images || !heights || !widths || !degr || !positions || !out)
+    return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  const int s = degr->scale, P = degr->lr_patch;
+  if (s < 1 || s > 4) return fail(ZOOM_ERR_INVALID_ARG, "scale must be in 1..4");
+  if (P != 3 && P != 5) return fail(ZOOM_ERR_UNSUPPORTED, "lr_patch must be 3 or 5");
+  if (!(degr->blur_sigma > 0.f)) return fail(ZOOM_ERR_INVALID_ARG, "blur_sigma must be > 0");
+  if (n_images < 1 || n_pairs < 1 || n_pairs > (1LL << 30))
+    return fail(ZOOM_ERR_INVALID_ARG, "n_images and n_pairs must be positive");
+  for (int m = 0; m < n_images; ++m) {
+    if (!hr_images[m]) return fail(ZOOM_ERR_INVALID_ARG, "NULL image pointer");
+    if (heights[m] / s < P || widths[m] / s < P)
+      return fail(ZOOM_ERR_INVALID_ARG, "training image smaller than one patch");
+  }
+  for (int64_t e = 0; e < n_pairs; ++e) {
+    int m = positions[3 * e], i = positions[3 * e + 1], j = positions[3 * e + 2];
+    if (m < 0 || m >= n_images || i < 0 || j < 0 || i + P > heights[m] / s ||
+        j + P > widths[m] / s)
+      return fail(ZOOM_ERR_INVALID_ARG, "position " + std::to_string(e) + " leaves its image");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  zoom_dict d = new zoom_dict_s();
+  d->ctx = ctx;
+  d->n = n_pairs;
+  d->P = P;
+  d->s = s;
+  d->d = P * P;
+  d->dpad = (d->d + 3) / 4 * 4;
+  d->PH = s * P;
+  d->ph2 = d->PH * d->PH;
+  d->ph2pad = (d->ph2 + 3) / 4 * 4;
+  d->blur_sigma = degr->blur_sigma;
+  {
+    Carver c(nullptr);
+    c.take<float>(n_pairs * d->d);
+    c.take<float>(n_pairs * d->dpad);
+    c.take<float>(n_pairs);
+    c.take<float>(n_pairs);
+    c.take<float>(n_pairs * d->ph2pad);
+    d->bytes = c.off + 256;
+  }
+  void* mem = zoom_alloc(ctx, d->bytes, st);
+  if (!mem) {
+    delete d;
+    return fail(ZOOM_ERR_OOM, "dictionary arrays");
+  }
+  Carver c(mem);
+  d->lr_pix = c.take<float>(n_pairs * d->d);
+  d->feat = c.take<float>(n_pairs * d->dpad);
+  d->mu = c.take<float>(n_pairs);
+  d->norm2 = c.take<float>(n_pairs);
+  d->hr_res = c.take<float>(n_pairs * d->ph2pad);
+
+  // scratch: LR images, pointer/width tables, positions
+  size_t lr_total = 0;
+  std::vector<size_t> lr_off(n_images);
+  for (int m = 0; m < n_images; ++m) {
+    lr_off[m] = lr_total;
+    lr_total += (size_t)(heights[m] / s) * (widths[m] / s);
+    lr_total = (lr_total + 63) / 64 * 64;
+  }
+  Carver sc(nullptr);
+  sc.take<float>(lr_total);
+  sc.take<const float*>(n_images);
+  sc.take<const float*>(n_images);
+  sc.take<int32_t>(n_images);
+  sc.take<int32_t>(n_images);
+  sc.take<int32_t>(n_pairs * 3);
+  Scratch scr(ctx, st);
+  if (!scr.get(sc.off + 256)) {
+    zoom_free(ctx, mem, d->bytes, st);
+    delete d;
+    return fail(ZOOM_ERR_OOM, "dictionary build scratch");
+  }
+  Carver s2(scr.p);
+  float* lr_all = s2.take<float>(lr_total);
+  const float** d_lr_ptr = s2.take<const float*>(n_images);
+  const float** d_hr_ptr = s2.take<const float*>(n_images);
+  int32_t* d_lr_w = s2.take<int32_t>(n_images);
+  int32_t* d_hr_w = s2.take<int32_t>(n_images);
+  int32_t* d_pos = s2.take<int32_t>(n_pairs * 3);
+  std::vector<const float*> h_lr_ptr(n_images), h_hr_ptr(n_images);
+  std::vector<int32_t> h_lr_w(n_images), h_hr_w(n_images);
+  zoom_status rc = ZOOM_OK;
+  for (int m = 0; m < n_images && rc == ZOOM_OK; ++m) {
+    float* lr = lr_all + lr_off[m];
+    h_lr_ptr[m] = lr;
+    h_hr_ptr[m] = hr_images[m];
+    h_lr_w[m] = widths[m] / s;
+    h_hr_w[m] = widths[m];
+    cudaError_t e = launch_degrade_exact(hr_images[m], heights[m], widths[m], s, degr->blur_sigma,
+                                         lr, st);
+    if (e != cudaSuccess) rc = fail(ZOOM_ERR_CUDA, std::string("degrade: ") + cudaGetErrorString(e));
+  }
+  if (rc == ZOOM_OK) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_lr_ptr, h_lr_ptr.data(), n_images * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_hr_ptr, h_hr_ptr.data(), n_images * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_lr_w, h_lr_w.data(), n_images * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_hr_w, h_hr_w.data(), n_images * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_pos, positions, n_pairs * 12, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_dict_gather(d_lr_ptr, d_lr_w, d_hr_ptr, d_hr_w, d_pos, n_pairs, P, s, d, st);
+    // the host vectors must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(ZOOM_ERR_CUDA, std::string("dictionary: ") + cudaGetErrorString(e));
+  }
+  if (rc != ZOOM_OK) {
+    zoom_free(ctx, mem, d->bytes, st);
+    delete d;
+    return rc;
+  }
+  *out = d;
+  return ZOOM_OK;
+}
+
+void zoom_dict_destroy(zoom_dict d) {
+  if (!d) return;
+  cudaSetDevice(d->ctx->device);
+  zoom_free(d->ctx, d->lr_pix, d->bytes, nullptr);
+  delete d;
+}
+
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale) {
+  if (!d) return fail(ZOOM_ERR_INVALID_ARG, "NULL dictionary");
+  if (n) *n = d->n;
+  if (patch) *patch = d->P;
+  if (scale) *scale = d->s;
+  return ZOOM_OK;
+}
+
+zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_res, void* stream) {
+  if (!d) return fail(ZOOM_ERR_INVALID_ARG, "NULL dictionary");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(d->ctx->device));
+  if (lr_pix)
+    ZCHECK_CUDA(cudaMemcpyAsync(lr_pix, d->lr_pix, d->n * d->d * 4, cudaMemcpyDeviceToHost, st));
+  if (mu) ZCHECK_CUDA(cudaMemcpyAsync(mu, d->mu, d->n * 4, cudaMemcpyDeviceToHost, st));
+  if (hr_res)
+    ZCHECK_CUDA(cudaMemcpy2DAsync(hr_res, d->ph2 * 4, d->hr_res, d->ph2pad * 4, d->ph2 * 4, d->n,
+                                  cudaMemcpyDeviceToHost, st));
+  ZCHECK_CUDA(cudaStreamSynchronize(st));
+  return ZOOM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// index
+// ---------------------------------------------------------------------------
+
+zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const float* alpha,
+                             const float* beta, void* stream, zoom_index* out) {
+  if (!d || !lsh || !alpha || !beta || !out) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  if (lsh->L < 1 || lsh->L > 32 || lsh->k < 1 || lsh->k > 32)
+    return fail(ZOOM_ERR_INVALID_ARG, "L and k must be in 1..32");
+  if (!(lsh->w > 0.f) || !isfinite(lsh->w)) return fail(ZOOM_ERR_INVALID_ARG, "w must be > 0");
+  if (lsh->min_table_hits < 1 || lsh->min_table_hits > lsh->L)
+    return fail(ZOOM_ERR_INVALID_ARG, "min_table_hits must be in 1..L");
+  if (lsh->max_candidates < 0 || lsh->max_candidates > 4096)
+    return fail(ZOOM_ERR_INVALID_ARG, "max_candidates must be in 0..4096");
+  if (lsh->max_candidates > 0)
+    return fail(ZOOM_ERR_UNSUPPORTED, "the candidate cap is not supported by this build");
+  const size_t smem = (size_t)lsh->L * lsh->k * (d->d + 1) * 4;
+  if (smem > 200 * 1024) return fail(ZOOM_ERR_INVALID_ARG, "L*k*(d+1) too large");
+  zoom_ctx ctx = d->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  const int64_t N = d->n;
+  const int L = lsh->L, k = lsh->k;
+  zoom_index ix = new zoom_index_s();
+  ix->dict = d;
+  ix->L = L;
+  ix->k = k;
+  ix->w = lsh->w;
+  ix->t = lsh->min_table_hits;
+  ix->cap = lsh->max_candidates;
+  {
+    Carver c(nullptr);
+    c.take<float>((size_t)L * k * d->d);
+    c.take<float>((size_t)L * k);
+    c.take<uint64_t>(N * L);
+    c.take<uint64_t>(N * L);
+    c.take<int32_t>((N + 1) * L);
+    c.take<int32_t>(N * L);
+    c.take<int32_t>(L);
+    ix->bytes = c.off + 256;
+  }
+  void* mem = zoom_alloc(ctx, ix->bytes, st);
+  if (!mem) {
+    delete ix;
+    return fail(ZOOM_ERR_OOM, "index arrays");
+  }
+  Carver c(mem);
+  ix->alpha = c.take<float>((size_t)L * k * d->d);
+  ix->beta = c.take<float>((size_t)L * k);
+  ix->dkeys = c.take<uint64_t>(N * L);
+  ix->ukeys = c.take<uint64_t>(N * L);
+  ix->offs = c.take<int32_t>((N + 1) * L);
+  ix->ids = c.take<int32_t>(N * L);
+  ix->nuniq = c.take<int32_t>(L);
+  zoom_status rc = ZOOM_OK;
+  cudaError_t e = cudaMemcpyAsync(ix->alpha, alpha, (size_t)L * k * d->d * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ix->beta, beta, (size_t)L * k * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = launch_hash(d->feat, d->dpad, d->d, N, ix->alpha, ix->beta, L, k, ix->w, ix->dkeys, st);
+  if (e == cudaSuccess) {
+    Scratch scr(ctx, st);
+    size_t sb = csr_scratch_bytes(N);
+    if (!scr.get(sb)) {
+      rc = fail(ZOOM_ERR_OOM, "index build scratch");
+    } else {
+      e = build_csr_tables(ix, scr.p, sb, st);
+    }
+    if (e == cudaSuccess && rc == ZOOM_OK) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess && rc == ZOOM_OK) rc = fail(ZOOM_ERR_CUDA, std::string("index: ") + cudaGetErrorString(e));
+  if (rc != ZOOM_OK) {
+    zoom_free(ctx, mem, ix->bytes, st);
+    delete ix;
+    return rc;
+  }
+  d->index_refs++;
+  *out = ix;
+  return ZOOM_OK;
+}
+
+void zoom_index_destroy(zoom_index ix) {
+  if (!ix) return;
+  cudaSetDevice(ix->dict->ctx->device);
+  ix->dict->index_refs--;
+  zoom_free(ix->dict->ctx, ix->alpha, ix->bytes, nullptr);
+  delete ix;
+}
+
+zoom_status zoom_index_export(zoom_index ix, uint64_t* keys, int32_t* n_bins, void* stream) {
+  if (!ix || !keys) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ix->dict->ctx->device));
+  ZCHECK_CUDA(cudaMemcpyAsync(keys, ix->dkeys, ix->dict->n * ix->L * 8, cudaMemcpyDeviceToHost, st));
+  if (n_bins) ZCHECK_CUDA(cudaMemcpyAsync(n_bins, ix->nuniq, ix->L * 4, cudaMemcpyDeviceToHost, st));
+  ZCHECK_CUDA(cudaStreamSynchronize(st));
+  return ZOOM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inference
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct QueryBufs {
+  float* feat;
+  float* mu;
+  float* norm2;
+  uint64_t* keys;
+  int32_t* nbr;
+  float* dist;
+  float* wgt;
+  int32_t* bucket_sum;
+};
+
+zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
+                            const zoom_upscale_params* prm, const QueryBufs& b, cudaStream_t st) {
+  zoom_dict d = ix->dict;
+  zoom_ctx ctx = d->ctx;
+  const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
+  zoom_stage_mark(ctx, 0, st);
+  cudaError_t e = launch_query_features(lr, h, w, d->P, d->dpad, b.feat, b.mu, b.norm2, st);
+  zoom_stage_mark(ctx, 1, st);
+  if (e == cudaSuccess)
+    e = launch_hash(b.feat, d->dpad, d->d, nq, ix->alpha, ix->beta, ix->L, ix->k, ix->w, b.keys, st);
+  zoom_stage_mark(ctx, 2, st);
+  if (e == cudaSuccess) e = launch_bucket_lookup(ix, b.keys, nq, b.bucket_sum, ctx->d_counters, st);
+  zoom_stage_mark(ctx, 3, st);
+  if (e == cudaSuccess)
+    e = launch_knn_exact(ix, b.feat, b.keys, nq, prm->K, b.nbr, b.dist, ctx->d_counters, st);
+  zoom_stage_mark(ctx, 4, st);
+  if (e == cudaSuccess)
+    e = launch_lle(d, b.feat, nq, b.nbr, b.dist, prm->K, prm->reg_rel, prm->fp64_cond_threshold,
+                   b.wgt, ctx->d_counters, st);
+  zoom_stage_mark(ctx, 5, st);
+  if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("query: ") + cudaGetErrorString(e));
+  return ZOOM_OK;
+}
+
+zoom_status begin_call(zoom_ctx ctx, int64_t nq, cudaStream_t st) {
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  for (int i = 0; i < 9; ++i) ctx->stage_rec[i] = false;
+  ZCHECK_CUDA(cudaMemsetAsync(ctx->d_counters, 0, CNT_N * sizeof(unsigned long long), st));
+  ZCHECK_CUDA(cudaEventRecord(ctx->ev0, st));
+  ctx->last_n_queries = nq;
+  ctx->timed = false;
+  return ZOOM_OK;
+}
+
+zoom_status end_call(zoom_ctx ctx, cudaStream_t st) {
+  ZCHECK_CUDA(cudaEventRecord(ctx->ev1, st));
+  ctx->timed = true;
+  return ZOOM_OK;
+}
+
+}  // namespace
+
+zoom_status zoom_query(zoom_index ix, const float* lr, int32_t h, int32_t w,
+                       const zoom_upscale_params* prm, uint64_t* keys, int32_t* nbr, float* dist,
+                       float* wgt, float* mu, int32_t* bucket_sum, void* stream) {
+  if (!ix || !lr || !nbr) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  zoom_dict d = ix->dict;
+  std::string why;
+  if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+  if (prm->precision != 0) return fail(ZOOM_ERR_UNSUPPORTED, "precision 1 not built yet");
+  if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
+  const int K = prm->K;
+  zoom_status rc = begin_call(d->ctx, nq, st);
+  if (rc != ZOOM_OK) return rc;
+  Carver c(nullptr);
+  c.take<float>(nq * d->dpad);
+  if (!mu) c.take<float>(nq);
+  if (!keys) c.take<uint64_t>(nq * ix->L);
+  if (!dist) c.take<float>(nq * K);
+  if (!wgt) c.take<float>(nq * K);
+  Scratch scr(d->ctx, st);
+  if (!scr.get(c.off + 256)) return fail(ZOOM_ERR_OOM, "query scratch");
+  Carver s2(scr.p);
+  QueryBufs b;
+  b.feat = s2.take<float>(nq * d->dpad);
+  b.mu = mu ? mu : s2.take<float>(nq);
+  b.norm2 = nullptr;
+  b.keys = keys ? keys : s2.take<uint64_t>(nq * ix->L);
+  b.dist = dist ? dist : s2.take<float>(nq * K);
+  b.wgt = wgt ? wgt : s2.take<float>(nq * K);
+  b.nbr = nbr;
+  b.bucket_sum = bucket_sum;
+  rc = run_query_steps(ix, lr, h, w, prm, b, st);
+  if (rc != ZOOM_OK) return rc;
+  return end_call(d->ctx, st);
+}
+
+zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt, const float* mu,
+                             int32_t h, int32_t w, int32_t K, float* hr, void* stream) {
+  if (!ix || !nbr || !wgt || !mu || !hr) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  zoom_dict d = ix->dict;
+  if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
+  if (K < 1 || K > 64) return fail(ZOOM_ERR_INVALID_ARG, "K must be in 1..64");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(d->ctx->device));
+  cudaError_t e = launch_overlap_add(nbr, wgt, mu, d->hr_res, d->ph2pad, K, h, w, d->s, d->P, hr, st);
+  if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("reconstruct: ") + cudaGetErrorString(e));
+  return ZOOM_OK;
+}
+
+static zoom_status run_backproject(zoom_ctx ctx, int s, float blur_sigma, const float* lr, int h,
+                                   int w, const zoom_upscale_params* prm, float* hr, float* tmp,
+                                   float* err, cudaStream_t st) {
+  // ping-pong between hr and tmp; an odd count ends with a copy back
+  float* a = hr;
+  float* b = tmp;
+  for (int it = 0; it < prm->bp_iters; ++it) {
+    cudaError_t e = launch_bp_iteration(a, b, lr, err, h, w, s, blur_sigma, prm->sigma_spatial,
+                                        prm->sigma_range, prm->bp_radius, st);
+    if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("backproject: ") + cudaGetErrorString(e));
+    std::swap(a, b);
+  }
+  if (a != hr)
+    ZCHECK_CUDA(cudaMemcpyAsync(hr, a, (size_t)s * h * s * w * 4, cudaMemcpyDeviceToDevice, st));
+  (void)ctx;
+  return ZOOM_OK;
+}
+
+zoom_status zoom_backproject(zoom_ctx ctx, const zoom_degradation* degr, const float* lr, int32_t h,
+                             int32_t w, const zoom_upscale_params* prm, float* hr, void* stream) {
+  if (!ctx || !degr || !lr || !prm || !hr) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  if (degr->scale < 1 || degr->scale > 4 || !(degr->blur_sigma > 0.f))
+    return fail(ZOOM_ERR_INVALID_ARG, "bad degradation");
+  if (h < 1 || w < 1) return fail(ZOOM_ERR_INVALID_ARG, "empty image");
+  if (prm->bp_iters < 0 || prm->bp_iters > 64 || prm->bp_radius < 1 || prm->bp_radius > 7 ||
+      !(prm->sigma_spatial > 0.f) || !(prm->sigma_range > 0.f))
+    return fail(ZOOM_ERR_INVALID_ARG, "bad back-projection parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  const int s = degr->scale;
+  Scratch scr(ctx, st);
+  Carver c(nullptr);
+  c.take<float>((size_t)s * h * s * w);
+  c.take<float>((size_t)h * w);
+  if (!scr.get(c.off + 256)) return fail(ZOOM_ERR_OOM, "backproject scratch");
+  Carver s2(scr.p);
+  float* tmp = s2.take<float>((size_t)s * h * s * w);
+  float* err = s2.take<float>((size_t)h * w);
+  return run_backproject(ctx, s, degr->blur_sigma, lr, h, w, prm, hr, tmp, err, st);
+}
+
+zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, int32_t scale,
+                         const zoom_upscale_params* prm, float* hr, void* stream) {
+  if (!ix || !lr || !hr) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  zoom_dict d = ix->dict;
+  std::string why;
+  if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+  if (prm->precision != 0) return fail(ZOOM_ERR_UNSUPPORTED, "precision 1 not built yet");
+  if (scale != d->s) return fail(ZOOM_ERR_INVALID_ARG, "scale differs from the dictionary's");
+  if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
+  const int K = prm->K, s = d->s;
+  zoom_status rc = begin_call(d->ctx, nq, st);
+  if (rc != ZOOM_OK) return rc;
+  Carver c(nullptr);
+  c.take<float>(nq * d->dpad);
+  c.take<float>(nq);
+  c.take<uint64_t>(nq * ix->L);
+  c.take<int32_t>(nq * K);
+  c.take<float>(nq * K);
+  c.take<float>(nq * K);
+  c.take<float>((size_t)s * h * s * w);
+  c.take<float>((size_t)h * w);
+  Scratch scr(d->ctx, st);
+  if (!scr.get(c.off + 256)) return fail(ZOOM_ERR_OOM, "upscale scratch");
+  Carver s2(scr.p);
+  QueryBufs b;
+  b.feat = s2.take<float>(nq * d->dpad);
+  b.mu = s2.take<float>(nq);
+  b.norm2 = nullptr;
+  b.keys = s2.take<uint64_t>(nq * ix->L);
+  b.nbr = s2.take<int32_t>(nq * K);
+  b.dist = s2.take<float>(nq * K);
+  b.wgt = s2.take<float>(nq * K);
+  b.bucket_sum = nullptr;
+  float* tmp = s2.take<float>((size_t)s * h * s * w);
+  float* err = s2.take<float>((size_t)h * w);
+  rc = run_query_steps(ix, lr, h, w, prm, b, st);
+  if (rc != ZOOM_OK) return rc;
+  cudaError_t e = launch_overlap_add(b.nbr, b.wgt, b.mu, d->hr_res, d->ph2pad, K, h, w, s, d->P, hr, st);
+  if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("overlap-add: ") + cudaGetErrorString(e));
+  zoom_stage_mark(d->ctx, 6, st);
+  rc = run_backproject(d->ctx, s, d->blur_sigma, lr, h, w, prm, hr, tmp, err, st);
+  if (rc != ZOOM_OK) return rc;
+  zoom_stage_mark(d->ctx, 7, st);
+  return end_call(d->ctx, st);
+}
+
+zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out) {
+  if (!ctx || !out) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  unsigned long long c[CNT_N];
+  ZCHECK_CUDA(cudaMemcpyAsync(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+  ZCHECK_CUDA(cudaStreamSynchronize(st));
+  memset(out, 0, sizeof(*out));
+  out->n_queries = ctx->last_n_queries;
+  out->mean_bucket_sum = ctx->last_n_queries ? (double)c[CNT_BUCKET_SUM] / ctx->last_n_queries : 0.0;
+  out->max_bucket_sum = (int64_t)c[CNT_BUCKET_MAX];
+  out->n_empty = (int64_t)c[CNT_EMPTY];
+  out->n_padded_queries = (int64_t)c[CNT_PADDED];
+  out->n_fp64_solves = (int64_t)c[CNT_FP64];
+  out->n_exact_match = (int64_t)c[CNT_EXACT];
+  out->n_filter_fallback = (int64_t)c[CNT_FALLBACK];
+  out->ms_total = 0.0;
+  for (int i = 0; i < 7; ++i) {
+    float ms = 0.f;
+    if (ctx->stage_rec[i] && ctx->stage_rec[i + 1] &&
+        cudaEventElapsedTime(&ms, ctx->stage_ev[i], ctx->stage_ev[i + 1]) == cudaSuccess)
+      out->ms_stage[i] = ms;
+    else
+      cudaGetLastError();
+  }
+  if (ctx->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) out->ms_total = ms;
+    else cudaGetLastError();
+  }
+  return ZOOM_OK;
+}
+
+zoom_status zoom_set_stage_timing(zoom_ctx ctx, int32_t enable) {
+  if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL context");
+  ctx->stage_timing = enable != 0;
+  return ZOOM_OK;
+}
+
+zoom_status zoom_sync_status(zoom_ctx ctx, void* stream) {
+  if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL context");
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  unsigned int v = 0;
+  ZCHECK_CUDA(cudaMemcpyAsync(&v, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
+  ZCHECK_CUDA(cudaStreamSynchronize(st));
+  if (v == 0) return ZOOM_OK;
+  ZCHECK_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
+  if (v == 1) return fail(ZOOM_ERR_TIMEOUT, "a device wait gave up");
+  return fail(ZOOM_ERR_DEVICE, "device status word " + std::to_string(v));
+}
+
+}  // extern "C"

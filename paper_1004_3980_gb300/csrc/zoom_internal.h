@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "zoom.h"
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+
+enum CounterSlot {
+  CNT_BUCKET_SUM = 0,   // sum over queries of sum_l |bin_l(q)|
+  CNT_BUCKET_MAX = 1,   // max over queries of the same
+  CNT_EMPTY = 2,        // queries with no candidate
+  CNT_PADDED = 3,       // queries with fewer than K candidates
+  CNT_FP64 = 4,         // LLE solves in FP64
+  CNT_EXACT = 5,        // exact-match (one-hot) queries
+  CNT_FALLBACK = 6,     // tensor-filter queries re-run exactly
+  CNT_N = 8
+};
+
+struct zoom_ctx_s {
+  int device = 0;
+  int n_sm = 0;
+  zoom_allocator alloc{};
+  bool has_alloc = false;
+  unsigned int* d_status = nullptr;       // device status word (0 = ok)
+  unsigned long long* d_counters = nullptr;  // [CNT_N]
+  int64_t last_n_queries = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  bool stage_timing = false;
+  cudaEvent_t stage_ev[9] = {};   // boundaries of the 7 stages (+1 spare)
+  bool stage_rec[9] = {};
+};
+
+// Records the boundary event of stage `i` when stage timing is on.
+void zoom_stage_mark(zoom_ctx ctx, int i, cudaStream_t st);
+
+struct zoom_dict_s {
+  zoom_ctx ctx = nullptr;
+  int64_t n = 0;
+  int P = 0, s = 0, d = 0, dpad = 0, PH = 0, ph2 = 0, ph2pad = 0;
+  float blur_sigma = 0.f;
+  float* lr_pix = nullptr;   // [N][d]
+  float* feat = nullptr;     // [N][dpad]  pixels - mu, zero padded
+  float* mu = nullptr;       // [N]
+  float* norm2 = nullptr;    // [N]  ||feat||^2
+  float* hr_res = nullptr;   // [N][ph2pad] HR patch - mu
+  size_t bytes = 0;
+  int index_refs = 0;
+};
+
+struct zoom_index_s {
+  zoom_dict dict = nullptr;
+  int L = 0, k = 0, t = 1, cap = 0;
+  float w = 0.f;
+  float* alpha = nullptr;    // [L*k][d]
+  float* beta = nullptr;     // [L*k]
+  uint64_t* dkeys = nullptr; // [N][L]
+  uint64_t* ukeys = nullptr; // [L][N]  bin keys, ascending (first nuniq[l] valid)
+  int32_t* offs = nullptr;   // [L][N+1] CSR offsets into ids
+  int32_t* ids = nullptr;    // [L][N]   entry IDs grouped by bin, ascending within a bin
+  int32_t* nuniq = nullptr;  // [L]
+  size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// host helpers (zoom_api.cu)
+// ---------------------------------------------------------------------------
+
+void zoom_set_error(const std::string& msg);
+void* zoom_alloc(zoom_ctx ctx, size_t bytes, cudaStream_t st);
+void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns cudaGetLastError() of its launches)
+// ---------------------------------------------------------------------------
+
+// dictionary / index build (kernels_build.cu)
+cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, float sigma, float* lr,
+                                 cudaStream_t st);
+cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_w,
+                               const float* const* d_hr_images, const int32_t* d_hr_w,
+                               const int32_t* d_pos, int64_t n, int P, int s, zoom_dict d,
+                               cudaStream_t st);
+cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const float* alpha,
+                        const float* beta, int L, int k, float w, uint64_t* keys, cudaStream_t st);
+cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t csr_scratch_bytes(int64_t n);
+
+// per-query steps (kernels_query.cu)
+cudaError_t launch_query_features(const float* lr, int h, int w, int P, int dpad, float* feat,
+                                  float* mu, float* norm2, cudaStream_t st);
+cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t nq,
+                                 int32_t* bucket_sum, unsigned long long* counters,
+                                 cudaStream_t st);
+cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
+                             int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                             cudaStream_t st);
+cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
+                       const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
+                       unsigned long long* counters, cudaStream_t st);
+
+// image steps (kernels_image.cu)
+cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float* mu,
+                               const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
+                               float* hr, cudaStream_t st);
+cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, float* err, int h,
+                                int w, int s, float blur_sigma, float sigma_sp, float sigma_r,
+                                int radius, cudaStream_t st);

@@ -1,0 +1,240 @@
+"""Python front end of the C ABI: torch CUDA tensors in, torch CUDA tensors
+out.  PyTorch supplies device memory (its caching allocator, handed to the
+library as the context allocator) and the current stream; every step of the
+method runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+STAGES = ("features", "hash", "lookup", "knn", "lle", "overlap_add", "backproject")
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+@dataclasses.dataclass
+class UpscaleParams:
+    """Inference parameters (see zoom_upscale_params in include/zoom.h)."""
+    K: int = 8
+    reg_rel: float = 1e-3
+    bp_iters: int = 5
+    sigma_spatial: float = 1.5
+    sigma_range: float = 0.1
+    bp_radius: int = 3
+    precision: int = 0
+    rerank_mult: int = 4
+    fp64_cond_threshold: float = 1e6
+
+    def c(self) -> capi.UpscaleParams:
+        return capi.UpscaleParams(self.K, self.reg_rel, self.bp_iters, self.sigma_spatial,
+                                  self.sigma_range, self.bp_radius, self.precision,
+                                  self.rerank_mult, self.fp64_cond_threshold)
+
+
+class Context:
+    """A library context on one CUDA device; device scratch memory comes from
+    PyTorch's caching allocator."""
+
+    def __init__(self, device: int = 0, torch_allocator: bool = True):
+        self.device = device
+        alloc = None
+        if torch_allocator:
+            def _a(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+                except Exception:  # the library reports ZOOM_ERR_OOM
+                    return None
+
+            def _f(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (capi.ALLOC_FN(_a), capi.FREE_FN(_f))
+            alloc = capi.Allocator(self._cb[0], self._cb[1], None)
+        self._alloc = alloc
+        h = C.c_void_p()
+        capi.call("zoom_ctx_create", device, C.byref(alloc) if alloc is not None else None,
+                  C.byref(h))
+        self.handle = h
+
+    def stats(self, stream=None) -> dict:
+        st = capi.Stats()
+        capi.call("zoom_get_stats", self.handle, _stream(stream), C.byref(st))
+        out = {f: getattr(st, f) for f, _ in capi.Stats._fields_ if f != "ms_stage"}
+        out["ms_stage"] = dict(zip(STAGES, list(st.ms_stage)[:len(STAGES)]))
+        return out
+
+    def set_stage_timing(self, enable: bool) -> None:
+        capi.call("zoom_set_stage_timing", self.handle, 1 if enable else 0)
+
+    def sync_status(self, stream=None) -> None:
+        capi.call("zoom_sync_status", self.handle, _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.device)
+            capi.lib().zoom_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Dictionary:
+    """LR/HR patch-pair dictionary built on the device (zoom_build_dictionary)."""
+
+    def __init__(self, ctx: Context, hr_images, positions, scale: int, patch: int,
+                 blur_sigma: float = 0.8, stream=None):
+        self.ctx = ctx
+        for t in hr_images:
+            _need(t, torch.float32, "hr image")
+        pos = np.ascontiguousarray(positions, dtype=np.int32)
+        n = len(hr_images)
+        ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hr_images])
+        hs = (C.c_int32 * n)(*[t.shape[0] for t in hr_images])
+        ws = (C.c_int32 * n)(*[t.shape[1] for t in hr_images])
+        degr = capi.Degradation(scale, patch, blur_sigma)
+        h = C.c_void_p()
+        capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), len(pos),
+                  pos.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream), C.byref(h))
+        self.handle = h
+        self.n, self.patch, self.scale, self.blur_sigma = len(pos), patch, scale, blur_sigma
+
+    def export(self, stream=None):
+        d, ph = self.patch ** 2, (self.scale * self.patch) ** 2
+        lr = np.empty((self.n, d), np.float32)
+        mu = np.empty(self.n, np.float32)
+        hr = np.empty((self.n, ph), np.float32)
+        capi.call("zoom_dict_export", self.handle, lr.ctypes.data, mu.ctypes.data, hr.ctypes.data,
+                  _stream(stream))
+        return lr, mu, hr
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.ctx.device)
+            capi.lib().zoom_dict_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Index:
+    """L-table p-stable LSH index over a dictionary (zoom_build_index)."""
+
+    def __init__(self, dictionary: Dictionary, L: int, k: int, w: float, alpha, beta,
+                 min_table_hits: int = 1, max_candidates: int = 0, stream=None):
+        self.dictionary = dictionary
+        a = np.ascontiguousarray(alpha, np.float32)
+        b = np.ascontiguousarray(beta, np.float32)
+        prm = capi.LshParams(L, k, w, min_table_hits, max_candidates)
+        h = C.c_void_p()
+        capi.call("zoom_build_index", dictionary.handle, C.byref(prm), a.ctypes.data, b.ctypes.data,
+                  _stream(stream), C.byref(h))
+        self.handle = h
+        self.L, self.k, self.w = L, k, w
+
+    def export_keys(self, stream=None):
+        keys = np.empty((self.dictionary.n, self.L), np.uint64)
+        nb = np.empty(self.L, np.int32)
+        capi.call("zoom_index_export", self.handle, keys.ctypes.data, nb.ctypes.data, _stream(stream))
+        return keys, nb
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.dictionary.ctx.device)
+            capi.lib().zoom_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def upscale(index: Index, lr: torch.Tensor, params: UpscaleParams | None = None,
+            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Zoom one LR image (CUDA float32 h x w) by the dictionary's scale."""
+    p = params or UpscaleParams()
+    _need(lr, torch.float32, "lr")
+    h, w = lr.shape
+    s = index.dictionary.scale
+    if out is None:
+        out = torch.empty((s * h, s * w), dtype=torch.float32, device=lr.device)
+    _need(out, torch.float32, "out")
+    cp = p.c()
+    capi.call("zoom_upscale", index.handle, _ptr(lr), h, w, s, C.byref(cp), _ptr(out), _stream(stream))
+    return out
+
+
+def query(index: Index, lr: torch.Tensor, params: UpscaleParams | None = None, stream=None) -> dict:
+    """Per-patch steps only: keys, neighbours, distances, weights, means."""
+    p = params or UpscaleParams()
+    _need(lr, torch.float32, "lr")
+    h, w = lr.shape
+    P = index.dictionary.patch
+    nq = (h - P + 1) * (w - P + 1)
+    dev = lr.device
+    keys = torch.empty((nq, index.L), dtype=torch.int64, device=dev)
+    nbr = torch.empty((nq, p.K), dtype=torch.int32, device=dev)
+    dist = torch.empty((nq, p.K), dtype=torch.float32, device=dev)
+    wgt = torch.empty((nq, p.K), dtype=torch.float32, device=dev)
+    mu = torch.empty(nq, dtype=torch.float32, device=dev)
+    bsum = torch.empty(nq, dtype=torch.int32, device=dev)
+    cp = p.c()
+    capi.call("zoom_query", index.handle, _ptr(lr), h, w, C.byref(cp), _ptr(keys), _ptr(nbr),
+              _ptr(dist), _ptr(wgt), _ptr(mu), _ptr(bsum), _stream(stream))
+    return {"keys": keys, "nbr": nbr, "dist": dist, "wgt": wgt, "mu": mu, "bucket_sum": bsum}
+
+
+def reconstruct(index: Index, nbr: torch.Tensor, wgt: torch.Tensor, mu: torch.Tensor, h: int, w: int,
+                stream=None) -> torch.Tensor:
+    """Eq. 14 blend + overlap average for given neighbours (no back-projection)."""
+    _need(nbr, torch.int32, "nbr")
+    _need(wgt, torch.float32, "wgt")
+    _need(mu, torch.float32, "mu")
+    s = index.dictionary.scale
+    out = torch.empty((s * h, s * w), dtype=torch.float32, device=nbr.device)
+    capi.call("zoom_reconstruct", index.handle, _ptr(nbr), _ptr(wgt), _ptr(mu), h, w, nbr.shape[1],
+              _ptr(out), _stream(stream))
+    return out
+
+
+def backproject(ctx: Context, lr: torch.Tensor, hr: torch.Tensor, scale: int,
+                params: UpscaleParams | None = None, blur_sigma: float = 0.8, stream=None) -> torch.Tensor:
+    """Back-projection iterations on hr (in place) against lr."""
+    p = params or UpscaleParams()
+    _need(lr, torch.float32, "lr")
+    _need(hr, torch.float32, "hr")
+    h, w = lr.shape
+    if hr.shape != (scale * h, scale * w):
+        raise ValueError("hr must be (scale*h, scale*w)")
+    degr = capi.Degradation(scale, 1, blur_sigma)
+    cp = p.c()
+    capi.call("zoom_backproject", ctx.handle, C.byref(degr), _ptr(lr), h, w, C.byref(cp), _ptr(hr),
+              _stream(stream))
+    return hr
