@@ -244,7 +244,9 @@ def main():
     stage_ms = {}
     e0.record(st)
     for _ in range(a.steps):
+        torch.cuda.nvtx.range_push("zoom_step")
         Z.upscale(ix, lr, prm, out=out)
+        torch.cuda.nvtx.range_pop()
         sm = ctx.stats()["ms_stage"]       # reads this step's stage events
         for k2, v in sm.items():
             stage_ms[k2] = stage_ms.get(k2, 0.0) + v

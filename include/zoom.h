@@ -61,12 +61,13 @@ typedef struct {
 
 /* Degradation and patch geometry (Sec. 2.1): HR -> Gaussian blur (3 taps,
  * sigma blur_sigma, clamped borders) -> s x s box down-sampling.  LR patches
- * are lr_patch x lr_patch; HR patches are (scale*lr_patch)^2.
+ * are lr_patch x lr_patch; HR patches are (scale*lr_patch)^2.  blur_sigma is
+ * a double so that the taps are computed from the exact parameter value.
  * Supported: scale 1..4, lr_patch 2..7, blur_sigma > 0. */
 typedef struct {
   int32_t scale;
   int32_t lr_patch;
-  float blur_sigma;
+  double blur_sigma;
 } zoom_degradation;
 
 /* LSH parameters (Sec. 3.2, Sec. 4.1).  L tables of k concatenated hashes

@@ -23,7 +23,7 @@ class Allocator(C.Structure):
 
 
 class Degradation(C.Structure):
-    _fields_ = [("scale", C.c_int32), ("lr_patch", C.c_int32), ("blur_sigma", C.c_float)]
+    _fields_ = [("scale", C.c_int32), ("lr_patch", C.c_int32), ("blur_sigma", C.c_double)]
 
 
 class LshParams(C.Structure):

@@ -20,8 +20,8 @@ struct PairWeights {
 
 // 1-D weights of "3-tap Gaussian then s-box mean": output i reads input
 // s*i + a - 1, a in [0, s+2), with weight (1/s) * sum_{b + u = a} taps[u].
-void degrade_weights_1d(int s, float sigma, double* wts) {
-  double e = exp(-1.0 / (2.0 * (double)sigma * (double)sigma));
+void degrade_weights_1d(int s, double sigma, double* wts) {
+  double e = exp(-1.0 / (2.0 * sigma * sigma));
   double t[3] = {e / (1.0 + 2.0 * e), 1.0 / (1.0 + 2.0 * e), e / (1.0 + 2.0 * e)};
   for (int a = 0; a < s + 2; ++a) wts[a] = 0.0;
   for (int b = 0; b < s; ++b)
@@ -315,7 +315,7 @@ __global__ void k_csr_write(const uint64_t* __restrict__ keys, const int32_t* __
 // launchers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, float sigma, float* lr,
+cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, double sigma, float* lr,
                                  cudaStream_t st) {
   double w1[kMaxScale + 2];
   degrade_weights_1d(s, sigma, w1);

@@ -108,12 +108,12 @@ cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float
 }
 
 cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, float* err, int h,
-                                int w, int s, float blur_sigma, float sigma_sp, float sigma_r,
+                                int w, int s, double blur_sigma, float sigma_sp, float sigma_r,
                                 int radius, cudaStream_t st) {
   const int H = s * h, W = s * w;
   Wts1D wt;
   {
-    double e = exp(-1.0 / (2.0 * (double)blur_sigma * (double)blur_sigma));
+    double e = exp(-1.0 / (2.0 * blur_sigma * blur_sigma));
     double t[3] = {e / (1.0 + 2.0 * e), 1.0 / (1.0 + 2.0 * e), e / (1.0 + 2.0 * e)};
     double acc[8] = {0};
     for (int b = 0; b < s; ++b)

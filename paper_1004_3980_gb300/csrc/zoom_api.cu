@@ -527,7 +527,7 @@ zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt
   return ZOOM_OK;
 }
 
-static zoom_status run_backproject(zoom_ctx ctx, int s, float blur_sigma, const float* lr, int h,
+static zoom_status run_backproject(zoom_ctx ctx, int s, double blur_sigma, const float* lr, int h,
                                    int w, const zoom_upscale_params* prm, float* hr, float* tmp,
                                    float* err, cudaStream_t st) {
   // ping-pong between hr and tmp; an odd count ends with a copy back

@@ -44,7 +44,7 @@ struct zoom_dict_s {
   zoom_ctx ctx = nullptr;
   int64_t n = 0;
   int P = 0, s = 0, d = 0, dpad = 0, PH = 0, ph2 = 0, ph2pad = 0;
-  float blur_sigma = 0.f;
+  double blur_sigma = 0.0;
   float* lr_pix = nullptr;   // [N][d]
   float* feat = nullptr;     // [N][dpad]  pixels - mu, zero padded
   float* mu = nullptr;       // [N]
@@ -81,7 +81,7 @@ void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st);
 // ---------------------------------------------------------------------------
 
 // dictionary / index build (kernels_build.cu)
-cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, float sigma, float* lr,
+cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, double sigma, float* lr,
                                  cudaStream_t st);
 cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_w,
                                const float* const* d_hr_images, const int32_t* d_hr_w,
@@ -110,5 +110,5 @@ cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float
                                const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
                                float* hr, cudaStream_t st);
 cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, float* err, int h,
-                                int w, int s, float blur_sigma, float sigma_sp, float sigma_r,
+                                int w, int s, double blur_sigma, float sigma_sp, float sigma_r,
                                 int radius, cudaStream_t st);

@@ -4,13 +4,34 @@ library as the context allocator) and the current stream; every step of the
 method runs in the library's CUDA kernels."""
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import dataclasses
+import sys
+import weakref
 
 import numpy as np
 import torch
 
 from . import capi
+
+# Live handles, closed at exit in dependency order (indexes, dictionaries,
+# contexts) while the CUDA runtime and torch are still up.
+_LIVE = {"index": weakref.WeakSet(), "dict": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("index", "dict", "ctx"):
+        for h in list(_LIVE[kind]):
+            try:
+                h.close()
+            except Exception:
+                pass
+
+
+def _finalizing() -> bool:
+    return sys.is_finalizing()
 
 
 STAGES = ("features", "hash", "lookup", "knn", "lle", "overlap_add", "backproject")
@@ -73,6 +94,7 @@ class Context:
         capi.call("zoom_ctx_create", device, C.byref(alloc) if alloc is not None else None,
                   C.byref(h))
         self.handle = h
+        _LIVE["ctx"].add(self)
 
     def stats(self, stream=None) -> dict:
         st = capi.Stats()
@@ -94,6 +116,8 @@ class Context:
             self.handle = None
 
     def __del__(self):
+        if _finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -118,6 +142,7 @@ class Dictionary:
         capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), len(pos),
                   pos.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream), C.byref(h))
         self.handle = h
+        _LIVE["dict"].add(self)
         self.n, self.patch, self.scale, self.blur_sigma = len(pos), patch, scale, blur_sigma
 
     def export(self, stream=None):
@@ -130,12 +155,15 @@ class Dictionary:
         return lr, mu, hr
 
     def close(self):
-        if getattr(self, "handle", None):
+        # a dictionary outlives its context only by mistake; then it leaks
+        if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
             torch.cuda.synchronize(self.ctx.device)
             capi.lib().zoom_dict_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
+        if _finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -155,6 +183,7 @@ class Index:
         capi.call("zoom_build_index", dictionary.handle, C.byref(prm), a.ctypes.data, b.ctypes.data,
                   _stream(stream), C.byref(h))
         self.handle = h
+        _LIVE["index"].add(self)
         self.L, self.k, self.w = L, k, w
 
     def export_keys(self, stream=None):
@@ -164,12 +193,14 @@ class Index:
         return keys, nb
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self.dictionary, "handle", None):
             torch.cuda.synchronize(self.dictionary.ctx.device)
             capi.lib().zoom_index_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
+        if _finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -81,8 +81,12 @@ def test_query_stages_match_oracle(built, oracle_queries):
     kmis = (keys != oq.keys).any(axis=1)
     assert not (kmis & ~qb).any()
     np.testing.assert_allclose(r["mu"].cpu().numpy(), oq.mu, atol=1e-6)
-    # bucket sizes (the similarity-check count of the paper) where keys agree
-    assert (r["bucket_sum"].cpu().numpy()[~qb] == oq.n_bucket[~qb]).all()
+    # bucket sizes (the similarity-check count of the paper) where keys agree;
+    # a boundary-affected dictionary entry may sit in a neighbouring bin
+    nb_dict_bnd = int((case.oindex.margin < 1e-5).sum())
+    bs = r["bucket_sum"].cpu().numpy()
+    assert (np.abs(bs - oq.n_bucket)[~qb] <= wl.L * max(nb_dict_bnd, 0)).all()
+    assert (bs[~qb] == oq.n_bucket[~qb]).mean() > 0.95
     ex = G.tie_or_boundary(oq, wl.K, case.oindex.margin)
     nbr = r["nbr"].cpu().numpy()
     bad = (nbr != oq.nbr[:, :wl.K]).any(axis=1) & ~ex
@@ -96,7 +100,7 @@ def test_query_stages_match_oracle(built, oracle_queries):
     assert np.abs(wgt[ok] - wk[ok]).max() < 2e-3
     st = ctx.stats()
     assert st["n_queries"] == len(nbr)
-    assert abs(st["mean_bucket_sum"] - oq.n_bucket.mean()) <= 1e-3 * oq.n_bucket.mean() + qb.sum() * 50
+    assert abs(st["mean_bucket_sum"] - oq.n_bucket.mean()) <= 1e-2 * oq.n_bucket.mean()
 
 
 def test_reconstruct_injected_neighbours(built, oracle_queries):
@@ -131,21 +135,26 @@ def test_upscale_end_to_end(built, oracle_queries):
     wl = case.wl
     oq, wk = oracle_queries
     import paper_1004_3980_gb300 as Z
-    hr = Z.upscale(ix, torch.from_numpy(case.lr).cuda(), G.params(wl)).cpu().numpy()
+    lr_t = torch.from_numpy(case.lr).cuda()
+    hr = Z.upscale(ix, lr_t, G.params(wl)).cpu().numpy()
     x0 = O.reconstruct(oq.nbr[:, :wl.K], wk, oq.mu, case.odict, wl.lr_h, wl.lr_w)
     ref = O.back_project(x0, case.lr, wl.scale, wl.blur_sigma, wl.bp_iters, wl.sigma_spatial,
                          wl.sigma_range, wl.bp_radius)
-    # pixels whose value depends on an excluded query (through the patches
-    # covering them and the back-projection window) are left out, and counted
+    # queries whose neighbour list differs (allowed only where a projection is
+    # on a bin boundary or distances tie) are left out together with every HR
+    # pixel they reach through their patch and the back-projection windows
+    nbr = Z.query(ix, lr_t, G.params(wl))["nbr"].cpu().numpy()
     ex = G.tie_or_boundary(oq, wl.K, case.oindex.margin)
+    differ = (nbr != oq.nbr[:, :wl.K]).any(axis=1)
+    assert not (differ & ~ex).any()
     P, s = wl.patch, wl.scale
     nw = wl.lr_w - P + 1
     mask = np.zeros_like(ref, bool)
     reach = wl.bp_iters * (wl.bp_radius + s + 1)
-    for q in np.flatnonzero(ex):
+    for q in np.flatnonzero(differ):
         i, j = divmod(q, nw)
         mask[max(0, s * i - reach):s * i + s * P + reach, max(0, s * j - reach):s * j + s * P + reach] = True
-    assert mask.mean() < 0.5
+    assert mask.mean() < 0.25, (differ.sum(), mask.mean())
     assert np.abs(hr - ref)[~mask].max() < 1e-3
     # the back-projection moves the degraded output toward the LR input
     r0 = np.linalg.norm(O.degrade(x0, s, 0.8) - case.lr)
@@ -180,19 +189,22 @@ def test_own_patches_give_one_hot_and_exact_hr(built):
 def test_small_candidate_sets_are_padded(built):
     # t = L (an ID must share the bin in every table) leaves some queries with
     # fewer than K candidates; they are padded with the nearest non-members.
-    case, _, _, _ = built
+    case, ctx, d, _ = built
     wl = case.wl
-    ctx, d, ix = G.gpu_build(case, min_table_hits=wl.L)
+    import paper_1004_3980_gb300 as Z
+    L, k, w = 4, 4, 0.1          # fine bins: few entries share a query's bin in all tables
+    alpha, beta = S.lsh_draws(23, L, k, wl.patch ** 2, w)
+    ix = Z.Index(d, L, k, w, alpha, beta, min_table_hits=L)
+    oindex = O.build_index(case.odict, alpha, beta, w, L, k)
     lr = case.lr[:20, :24]
-    r = __import__("paper_1004_3980_gb300").query(ix, torch.from_numpy(np.ascontiguousarray(lr)).cuda(),
-                                                  G.params(wl, K=8))
+    r = Z.query(ix, torch.from_numpy(np.ascontiguousarray(lr)).cuda(), G.params(wl, K=8))
     nbr = r["nbr"].cpu().numpy()
-    oq = O.query(lr, case.odict, case.oindex, 9, wl.reg_rel, min_hits=wl.L)
-    ex = G.tie_or_boundary(oq, 8, case.oindex.margin)
+    oq = O.query(lr, case.odict, oindex, 9, wl.reg_rel, min_hits=L)
+    ex = G.tie_or_boundary(oq, 8, oindex.margin)
     assert (oq.n_padded > 0).any()
     bad = (nbr != oq.nbr[:, :8]).any(axis=1) & ~ex
     assert not bad.any()
-    assert ctx.stats()["n_padded_queries"] == int((oq.n_padded[:] > 0).sum()) or ex.any()
+    assert ctx.stats()["n_padded_queries"] == int((oq.n_cand < 8).sum())
 
 
 @pytest.mark.parametrize("K", [1, 12])
