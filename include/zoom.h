@@ -92,7 +92,12 @@ typedef struct {
  * precision: 0 = exact FP32 neighbour search; 1 = BF16 tensor-core distance
  * filter keeping the rerank_mult*K best, then FP32 exact rerank.
  * fp64_cond_threshold: the LLE solve runs in FP64 for a query whose
- * condition bound (trace(G) + eps) / eps exceeds it. */
+ * condition bound (trace(G) + eps) / eps exceeds it.
+ * search (precision 0 only): 0 = automatic, 1 = SIMT scan of the dictionary
+ * in FP32 difference form, 2 = tensor-core distance filter with a proven
+ * exact FP32 rerank (queries it cannot settle re-run the SIMT scan).  All
+ * three give the same neighbours.  Precision 1 always uses the tensor cores;
+ * it needs rerank_mult * K <= 32. */
 typedef struct {
   int32_t K;
   float reg_rel;
@@ -103,6 +108,7 @@ typedef struct {
   int32_t precision;
   int32_t rerank_mult;
   double fp64_cond_threshold;
+  int32_t search;
 } zoom_upscale_params;
 
 /* Counters of the last zoom_query / zoom_upscale on a context (read after

@@ -27,6 +27,7 @@ SOURCES = [
     "kernels_build.cu",
     "kernels_query.cu",
     "kernels_image.cu",
+    "kernels_tc.cu",
 ]
 HEADERS = ["zoom_internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -35,7 +35,7 @@ class UpscaleParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("reg_rel", C.c_float), ("bp_iters", C.c_int32),
                 ("sigma_spatial", C.c_float), ("sigma_range", C.c_float), ("bp_radius", C.c_int32),
                 ("precision", C.c_int32), ("rerank_mult", C.c_int32),
-                ("fp64_cond_threshold", C.c_double)]
+                ("fp64_cond_threshold", C.c_double), ("search", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -119,11 +119,21 @@ __global__ __launch_bounds__(KNN_THREADS) void k_knn_exact(
     const float* __restrict__ qfeat, int dpad, int64_t nq, const uint64_t* __restrict__ qkeys,
     const float* __restrict__ dfeat, int64_t N, const uint64_t* __restrict__ dkeys, int L, int tmin,
     int K, int32_t* __restrict__ nbr, float* __restrict__ dist,
-    unsigned long long* __restrict__ counters) {
+    unsigned long long* __restrict__ counters, const int32_t* __restrict__ qidx,
+    const unsigned long long* __restrict__ qcount) {
   constexpr int DP = (D + 3) / 4 * 4;
   __shared__ __align__(16) float tile[KNN_TN * DP];
-  const int64_t q = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
-  const bool active = q < nq;
+  // with qidx, thread i handles query qidx[i] for i < *qcount (queries that
+  // another search path could not settle)
+  const int64_t slot = (int64_t)blockIdx.x * KNN_THREADS + threadIdx.x;
+  int64_t q = slot;
+  bool active = q < nq;
+  if (qidx) {
+    const int64_t cnt = (int64_t)*qcount;
+    if ((int64_t)blockIdx.x * KNN_THREADS >= cnt) return;   // whole block idle
+    active = slot < cnt;
+    q = active ? qidx[slot] : 0;
+  }
   float qv[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) qv[i] = active ? qfeat[q * dpad + i] : 0.f;
@@ -329,17 +339,17 @@ __global__ __launch_bounds__(128) void k_lle(const float* __restrict__ qfeat, in
 template <int D>
 cudaError_t knn_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
                            int K, int32_t* nbr, float* dist, unsigned long long* counters,
-                           cudaStream_t st) {
+                           const int32_t* qidx, const unsigned long long* qcount, cudaStream_t st) {
   zoom_dict d = ix->dict;
   int blocks = (int)((nq + KNN_THREADS - 1) / KNN_THREADS);
   if (K <= 8)
     k_knn_exact<D, 8><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
                                                      ix->dkeys, ix->L, ix->t, K, nbr, dist,
-                                                     counters);
+                                                     counters, qidx, qcount);
   else
     k_knn_exact<D, 16><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
                                                       ix->dkeys, ix->L, ix->t, K, nbr, dist,
-                                                      counters);
+                                                      counters, qidx, qcount);
   return cudaGetLastError();
 }
 
@@ -383,9 +393,12 @@ cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t n
 
 cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
                              int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                             const int32_t* qidx, const unsigned long long* qcount,
                              cudaStream_t st) {
-  if (ix->dict->d == 9) return knn_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, st);
-  if (ix->dict->d == 25) return knn_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, st);
+  if (ix->dict->d == 9)
+    return knn_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, qidx, qcount, st);
+  if (ix->dict->d == 25)
+    return knn_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, qidx, qcount, st);
   return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,767 @@
+// Neighbour search on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The candidate set of a query is, at the bin widths of the workloads, most
+// of the dictionary, so the search is a dense (queries x dictionary)
+// contraction.  A tensor-core pass computes, for every (query, entry) pair,
+//   acc = ||c||^2 - 2 q.c        (d~ = ||q||^2 + acc approximates |q - c|^2)
+// and keeps per query the MC smallest d~ of every dictionary split.  A
+// rerank kernel then computes the exact FP32 difference-form distance of the
+// kept entries, tests LSH membership and selects the K nearest members.
+//
+// Exact form (FP16, 3 terms): q = q_hi + q_lo, c = c_hi + c_lo (fp16 pairs),
+//   A row = [q_hi | q_lo | q_hi | 1 | 1 | 0 0 0]            (K = 80)
+//   B row = [-2c_hi | -2c_hi | -2c_lo | n_hi | n_lo | 0 0 0]
+// so acc misses only -2 q_lo.c_lo (about 2^-22 relative).  With an error
+// bound delta on |d~ - d|, a query whose K-th exact distance D_K satisfies
+// T - delta > D_K (T: smallest list threshold over the splits) provably has
+// every nearer member inside the lists; other queries are re-run by the
+// exact SIMT scan.  The result equals the exact scan's.
+// Precision form (BF16, 1 term): A = [q | 1 1 1 | 0..], B = [-2c | n1 n2 n3 | 0..]
+// (K = 32); the rerank takes the best rerank_mult*K of the merged lists.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <float.h>
+
+#include "device_common.cuh"
+#include "zoom_internal.h"
+
+namespace {
+
+constexpr int TC_THREADS = 320;   // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+constexpr int TC_STAGES = 4;
+constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
+constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of `parity` to complete.  Gives up after kWaitNs (or
+// 2^30 polls), or as soon as another role gave up: then it raises the shared
+// abort flag, records ZOOM_ERR_TIMEOUT in the status word and returns false.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                       unsigned int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kWaitNs) break;
+    }
+  }
+  *abort_flag = 1;
+  atomicExch(status, 1u);
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M = N = 128, kind::f16 (fp16 or bf16 in,
+// fp32 accumulate).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes stored as 128 contiguous bytes; `lbo` = byte distance
+// between core matrices adjacent along K, `sbo` = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of sm_100-family tcgen05
+  return d;                // base offset 0, absolute LBO mode, no swizzle
+}
+
+// Instruction descriptor of kind::f16: D fp32, A and B of the same type
+// (fp16: 0, bf16: 1), both K-major, M = N = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_type) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(TC_ROWS >> 3) << 17) |
+         ((uint32_t)(TC_ROWS >> 4) << 24);
+}
+
+struct TcArgs {
+  const uint16_t* qop;   // [q_tiles (even)][KC][128][8] fp16/bf16 bits
+  const float* qn;       // [nq] ||q||^2 (FP32)
+  const uint16_t* dop;   // [d_tiles][KC][128][8]
+  int64_t nq;
+  int64_t nd;
+  int nq_pairs;          // ceil(nq / 256)
+  int nd_tiles;          // ceil(nd / 128)
+  int nsplit;
+  int tiles_per_split;
+  float* out_d;          // [nsplit][nq][MC] d~ ascending
+  int32_t* out_id;       // [nsplit][nq][MC]
+  unsigned int* status;
+};
+
+template <int MC>
+__device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float v, int id, float& thr) {
+  // v < ld[MC-1]: insert keeping ascending order
+  bool done = false;
+#pragma unroll
+  for (int j = MC - 1; j > 0; --j) {
+    if (!done) {
+      if (v < ld[j - 1]) {
+        ld[j] = ld[j - 1];
+        li[j] = li[j - 1];
+      } else {
+        ld[j] = v;
+        li[j] = id;
+        done = true;
+      }
+    }
+  }
+  if (!done) {
+    ld[0] = v;
+    li[0] = id;
+  }
+  thr = ld[MC - 1];
+}
+
+template <int KC, int MC, uint32_t AB_TYPE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
+  constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
+  constexpr int kKSteps = KC / 2;                     // MMA K = 16 = two 8-element chunks
+  constexpr uint32_t kIdesc = instr_desc(AB_TYPE);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;                                  // 2 query tiles
+  unsigned char* sB = smem + 2 * kTileBytes;                 // TC_STAGES dictionary tiles
+  uint64_t* bars = (uint64_t*)(sB + TC_STAGES * kTileBytes);
+  uint64_t* a_full = bars + 0;
+  uint64_t* a_empty = bars + 1;
+  uint64_t* b_full = bars + 2;                 // [TC_STAGES]
+  uint64_t* b_empty = b_full + TC_STAGES;      // [TC_STAGES]
+  uint64_t* acc_full = b_empty + TC_STAGES;    // [2]
+  uint64_t* acc_empty = acc_full + 2;          // [2]
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    mbar_init(a_empty, 1);
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(b_full + s, 1);
+      mbar_init(b_empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + b, 1);
+      mbar_init(acc_empty + b, 256);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int n_items = a.nsplit * a.nq_pairs;
+
+  if (warp == 0) {
+    // ---------------- producer: bulk copies of operand tiles ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, a_phase = 0;
+      bool first = true;
+      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
+        const int t0 = split * a.tiles_per_split;
+        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+        if (!first) {
+          if (!mbar_wait(a_empty, a_phase, abort_flag, a.status)) break;
+          a_phase ^= 1u;
+        }
+        first = false;
+        mbar_arrive_expect_tx(a_full, 2 * kTileBytes);
+        bulk_g2s(sA, (const unsigned char*)a.qop + (size_t)qp * 2 * kTileBytes, 2 * kTileBytes, a_full);
+        for (int t = t0; t < t1; ++t) {
+          if (!mbar_wait(b_empty + stage, phase ^ 1u, abort_flag, a.status)) break;
+          mbar_arrive_expect_tx(b_full + stage, kTileBytes);
+          bulk_g2s(sB + stage * kTileBytes, (const unsigned char*)a.dop + (size_t)t * kTileBytes,
+                   kTileBytes, b_full + stage);
+          if (++stage == TC_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issue (one thread) ----------------
+    if (lane == 0) {
+      int stage = 0, buf = 0, items = 0;
+      uint32_t phase = 0, a_phase = 0;
+      uint32_t accp[2] = {0u, 0u};
+      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        const int split = item / a.nq_pairs;
+        const int t0 = split * a.tiles_per_split;
+        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+        if (!mbar_wait(a_full, a_phase, abort_flag, a.status)) break;
+        a_phase ^= 1u;
+        tc_fence_after();
+        bool ok = true;
+        for (int t = t0; t < t1; ++t) {
+          if (!mbar_wait(b_full + stage, phase, abort_flag, a.status) ||
+              !mbar_wait(acc_empty + buf, accp[buf] ^ 1u, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b_base = smem_u32(sB + stage * kTileBytes);
+#pragma unroll
+          for (int qt = 0; qt < 2; ++qt) {
+            const uint32_t a_base = smem_u32(sA + qt * kTileBytes);
+            const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
+#pragma unroll
+            for (int ks = 0; ks < kKSteps; ++ks) {
+              const uint64_t ad = smem_desc(a_base + ks * 2 * TC_ROWS * 16, TC_ROWS * 16, 128);
+              const uint64_t bd = smem_desc(b_base + ks * 2 * TC_ROWS * 16, TC_ROWS * 16, 128);
+              mma_f16(d_addr, ad, bd, kIdesc, ks > 0 ? 1u : 0u);
+            }
+          }
+          mma_commit(b_empty + stage);
+          mma_commit(acc_full + buf);
+          accp[buf] ^= 1u;
+          buf ^= 1;
+          if (++stage == TC_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        mma_commit(a_empty);
+        ++items;
+        if (!ok) break;
+      }
+      // the last item's release of the query tiles is never consumed by the
+      // producer: wait for it so no tensor-core arrival is pending at exit
+      if (items > 0) mbar_wait(a_empty, (uint32_t)(items - 1) & 1u, abort_flag, a.status);
+    }
+  } else {
+    // ---------------- epilogue: per-query best lists ----------------
+    const int ew = warp - 2;            // 0..7
+    const int qt = ew >> 2;             // query tile within the pair
+    const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;   // row in the 128-row tile
+    int buf = 0;
+    uint32_t accp[2] = {0u, 0u};
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;   // warp-uniform exit
+      const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
+      const int t0 = split * a.tiles_per_split;
+      const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+      const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
+      const bool valid = q < a.nq;
+      const float qn = valid ? a.qn[q] : 0.f;
+      float ld[MC];
+      int li[MC];
+#pragma unroll
+      for (int j = 0; j < MC; ++j) {
+        ld[j] = FLT_MAX;
+        li[j] = -1;
+      }
+      float thr = FLT_MAX;   // in acc units: d~ - ||q||^2
+      bool ok = true;
+      for (int t = t0; t < t1; ++t) {
+        // every lane polls, then the warp agrees (and reconverges) before the
+        // warp-collective TMEM loads
+        const bool w = __all_sync(0xffffffffu, mbar_wait(acc_full + buf, accp[buf], abort_flag, a.status));
+        if (!w) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tmem_ld32(tb + c * 32, v);
+          float m = v[0];
+#pragma unroll
+          for (int j = 1; j < 32; ++j) m = fminf(m, v[j]);
+          if (m < thr) {
+            const int col0 = t * TC_ROWS + c * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (v[j] < thr) list_push<MC>(ld, li, v[j], col0 + j, thr);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(acc_empty + buf);
+        accp[buf] ^= 1u;
+        buf ^= 1;
+      }
+      if (!ok) break;
+      if (valid) {
+        float* od = a.out_d + ((int64_t)split * a.nq + q) * MC;
+        int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+          const bool real = li[j] >= 0 && li[j] < a.nd;
+          od[j] = real ? qn + ld[j] : FLT_MAX;
+          oi[j] = real ? li[j] : -1;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation
+// ---------------------------------------------------------------------------
+
+// Offset (in 16-bit elements) of element k of row r in the tiled layout
+// [tile][kc][128][8].
+__device__ __forceinline__ int64_t op_off(int64_t r, int k, int KC) {
+  return (r / TC_ROWS) * ((int64_t)KC * TC_ROWS * 8) + (int64_t)(k >> 3) * (TC_ROWS * 8) +
+         (r % TC_ROWS) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint16_t h_bits(__half h) { return __half_as_ushort(h); }
+__device__ __forceinline__ uint16_t b_bits(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
+
+// role 0: query rows, role 1: dictionary rows.  Rows in [n, n_rows) are
+// padding: queries get zeros, dictionary entries a huge norm so that they
+// never rank.
+template <int D>
+__global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
+                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
+  constexpr int KC = 10;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  uint16_t row[80];
+#pragma unroll
+  for (int k = 0; k < 80; ++k) row[k] = 0;
+  if (r < n) {
+    float n2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float v = feat[r * dpad + i];
+      n2 = fmaf(v, v, n2);
+      const __half hi = __float2half_rn(v);
+      const __half lo = __float2half_rn(v - __half2float(hi));
+      if (role == 0) {
+        row[i] = h_bits(hi);
+        row[25 + i] = h_bits(lo);
+        row[50 + i] = h_bits(hi);
+      } else {
+        const __half mh = __float2half_rn(-2.f * __half2float(hi));
+        row[i] = h_bits(mh);
+        row[25 + i] = h_bits(mh);
+        row[50 + i] = h_bits(__float2half_rn(-2.f * __half2float(lo)));
+      }
+    }
+    if (role == 0) {
+      row[75] = h_bits(__float2half_rn(1.f));
+      row[76] = h_bits(__float2half_rn(1.f));
+    } else {
+      const __half nh = __float2half_rn(n2);
+      row[75] = h_bits(nh);
+      row[76] = h_bits(__float2half_rn(n2 - __half2float(nh)));
+    }
+    if (norm_out) norm_out[r] = n2;
+  } else if (role == 1) {
+    row[75] = h_bits(__float2half_rn(60000.f));
+  }
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) {
+    uint4 pk;
+    pk.x = (uint32_t)row[kc * 8 + 0] | ((uint32_t)row[kc * 8 + 1] << 16);
+    pk.y = (uint32_t)row[kc * 8 + 2] | ((uint32_t)row[kc * 8 + 3] << 16);
+    pk.z = (uint32_t)row[kc * 8 + 4] | ((uint32_t)row[kc * 8 + 5] << 16);
+    pk.w = (uint32_t)row[kc * 8 + 6] | ((uint32_t)row[kc * 8 + 7] << 16);
+    *reinterpret_cast<uint4*>(op + op_off(r, kc * 8, KC)) = pk;
+  }
+}
+
+template <int D>
+__global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
+                               int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
+  constexpr int KC = 4;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  uint16_t row[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) row[k] = 0;
+  if (r < n) {
+    float n2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float v = feat[r * dpad + i];
+      n2 = fmaf(v, v, n2);
+      row[i] = b_bits(__float2bfloat16_rn(role == 0 ? v : -2.f * v));
+    }
+    if (role == 0) {
+      row[D] = row[D + 1] = row[D + 2] = b_bits(__float2bfloat16_rn(1.f));
+    } else {
+      const __nv_bfloat16 n1 = __float2bfloat16_rn(n2);
+      const float r1 = n2 - __bfloat162float(n1);
+      const __nv_bfloat16 nb = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 nc = __float2bfloat16_rn(r1 - __bfloat162float(nb));
+      row[D] = b_bits(n1);
+      row[D + 1] = b_bits(nb);
+      row[D + 2] = b_bits(nc);
+    }
+    if (norm_out) norm_out[r] = n2;
+  } else if (role == 1) {
+    row[D] = b_bits(__float2bfloat16_rn(60000.f));
+  }
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) {
+    uint4 pk;
+    pk.x = (uint32_t)row[kc * 8 + 0] | ((uint32_t)row[kc * 8 + 1] << 16);
+    pk.y = (uint32_t)row[kc * 8 + 2] | ((uint32_t)row[kc * 8 + 3] << 16);
+    pk.z = (uint32_t)row[kc * 8 + 4] | ((uint32_t)row[kc * 8 + 5] << 16);
+    pk.w = (uint32_t)row[kc * 8 + 6] | ((uint32_t)row[kc * 8 + 7] << 16);
+    *reinterpret_cast<uint4*>(op + op_off(r, kc * 8, KC)) = pk;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rerank: exact FP32 distances of the listed entries in ascending d~ order,
+// LSH membership, K nearest members; exactness proof or fallback flag.
+// ---------------------------------------------------------------------------
+template <int D, int MC, int KMAX>
+__global__ __launch_bounds__(128) void k_rerank(
+    const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
+    const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
+    const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ ld,
+    const int32_t* __restrict__ li, int nsplit, int K, int exact, int max_examine, float eps_rel,
+    int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ fb_list,
+    unsigned long long* __restrict__ counters) {
+  constexpr int SMAX = 8;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  float qv[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) qv[i] = qfeat[q * dpad + i];
+  const float qn = qn_arr[q];
+  // merge heads of the per-split lists (each ascending in d~)
+  int head[SMAX];
+  float T = FLT_MAX;
+#pragma unroll
+  for (int s = 0; s < SMAX; ++s) {
+    head[s] = 0;
+    if (s < nsplit) T = fminf(T, ld[((int64_t)s * nq + q) * MC + MC - 1]);
+  }
+  float bd[KMAX];
+  int bi[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    bd[j] = FLT_MAX;
+    bi[j] = INT_MAX;
+  }
+  int members = 0, examined = 0;
+  float delta = 0.f, dK = FLT_MAX;
+  const float qnorm = sqrtf(qn);
+  bool flagged = false;
+  while (true) {
+    // next entry in ascending d~ over the splits
+    float best = FLT_MAX;
+    int bs = -1;
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      if (s < nsplit && head[s] < MC) {
+        const float v = ld[((int64_t)s * nq + q) * MC + head[s]];
+        if (v < best) {
+          best = v;
+          bs = s;
+        }
+      }
+    }
+    if (bs < 0 || best == FLT_MAX) break;
+    if (exact) {
+      // stop once no further listed entry can beat the K-th exact distance
+      if (members >= K && best - delta > dK) break;
+    } else if (examined >= max_examine) {
+      break;
+    }
+    const int id = li[((int64_t)bs * nq + q) * MC + head[bs]];
+    ++head[bs];
+    ++examined;
+    if (id < 0 || id >= nd) continue;
+    int hits = 0;
+    for (int l = 0; l < L; ++l) hits += (qkeys[q * L + l] == dkeys[(int64_t)id * L + l]) ? 1 : 0;
+    if (hits < tmin) continue;
+    float dd = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float df = qv[i] - dfeat[(int64_t)id * dpad + i];
+      dd = fmaf(df, df, dd);
+    }
+    ++members;
+    // insert (dd, id) into the sorted top-K
+    float wd = bd[0];
+    int wi = bi[0];
+#pragma unroll
+    for (int j = 1; j < KMAX; ++j)
+      if (j == K - 1) {
+        wd = bd[j];
+        wi = bi[j];
+      }
+    if (dd < wd || (dd == wd && id < wi)) {
+      bool done = false;
+#pragma unroll
+      for (int j = KMAX - 1; j > 0; --j) {
+        if (j < K && !done) {
+          if (dd < bd[j - 1] || (dd == bd[j - 1] && id < bi[j - 1])) {
+            bd[j] = bd[j - 1];
+            bi[j] = bi[j - 1];
+          } else {
+            bd[j] = dd;
+            bi[j] = id;
+            done = true;
+          }
+        }
+      }
+      if (!done) {
+        bd[0] = dd;
+        bi[0] = id;
+      }
+    }
+    if (members >= K) {
+      dK = bd[0];
+#pragma unroll
+      for (int j = 1; j < KMAX; ++j)
+        if (j == K - 1) dK = bd[j];
+    }
+    if (exact && members >= K) {
+      // |d~ - d| bound for any entry that could beat dK: such an entry has
+      // ||c|| <= ||q|| + sqrt(dK); the bound covers the FP16 split, the
+      // tensor-core FP32 accumulation and the FP32 rerank arithmetic.
+      const float rc = qnorm + sqrtf(dK) * 1.001f + 1e-6f;
+      delta = eps_rel * (6.f * qnorm * rc + rc * rc + qn) + 4e-6f * dK + 1e-12f;
+    }
+  }
+  if (members < K) {
+    flagged = true;
+  } else if (exact) {
+    if (!(T - delta > dK)) flagged = true;
+  }
+  if (flagged) {
+    const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
+    fb_list[slot] = (int32_t)q;
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j)
+    if (j < K) {
+      nbr[q * K + j] = bi[j];
+      dist[q * K + j] = bd[j];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+int64_t tc_rows_padded(int64_t n, bool even_tiles) {
+  int64_t t = (n + TC_ROWS - 1) / TC_ROWS;
+  if (even_tiles && (t & 1)) ++t;
+  if (t == 0) t = even_tiles ? 2 : 1;
+  return t * TC_ROWS;
+}
+
+cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
+                           int precision, uint16_t* op, float* norm_out, cudaStream_t st) {
+  const int blocks = (int)((n_rows + 127) / 128);
+  if (d == 25) {
+    if (precision == 0)
+      k_operand_f16x3<25><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
+    else
+      k_operand_bf16<25><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
+  } else if (d == 9) {
+    if (precision == 0)
+      k_operand_f16x3<9><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
+    else
+      k_operand_bf16<9><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+size_t tc_smem_bytes(int precision) {
+  const int KC = precision == 0 ? 10 : 4;
+  // alignment pad + operand tiles + barriers, plus 64 KB of slack so that
+  // every address a descriptor of these tiles can form stays inside the
+  // allocation (one CTA per SM either way)
+  return 1024 + (size_t)(2 + TC_STAGES) * KC * TC_ROWS * 16 + 256 + 64 * 1024;
+}
+
+int tc_list_size(int precision, int K, int rerank_mult) {
+  if (precision == 0) return K <= 12 ? 16 : 32;
+  return rerank_mult * K <= 16 ? 16 : 32;
+}
+
+template <int KC, int MC, uint32_t T>
+static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_knn_tc<KC, MC, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, TC_THREADS, smem, st>>>(args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
+                          int64_t nd, int precision, int MC, int nsplit, int grid, float* out_d,
+                          int32_t* out_id, unsigned int* status, cudaStream_t st) {
+  TcArgs a;
+  a.qop = qop;
+  a.qn = qn;
+  a.dop = dop;
+  a.nq = nq;
+  a.nd = nd;
+  a.nq_pairs = (int)((nq + 2 * TC_ROWS - 1) / (2 * TC_ROWS));
+  a.nd_tiles = (int)((nd + TC_ROWS - 1) / TC_ROWS);
+  a.nsplit = nsplit;
+  a.tiles_per_split = (a.nd_tiles + nsplit - 1) / nsplit;
+  a.out_d = out_d;
+  a.out_id = out_id;
+  a.status = status;
+  const size_t smem = tc_smem_bytes(precision);
+  const int items = a.nsplit * a.nq_pairs;
+  grid = grid < items ? grid : items;
+  if (precision == 0) {
+    if (MC == 16) return run_tc_kernel<10, 16, 0>(a, grid, smem, st);
+    return run_tc_kernel<10, 32, 0>(a, grid, smem, st);
+  }
+  if (MC == 16) return run_tc_kernel<4, 16, 1>(a, grid, smem, st);
+  return run_tc_kernel<4, 32, 1>(a, grid, smem, st);
+}
+
+template <int D, int MC>
+static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn, const uint64_t* qkeys,
+                            int64_t nq, const float* dfeat, const uint64_t* dkeys, int64_t nd, int L,
+                            int tmin, const float* ld, const int32_t* li, int nsplit, int exact,
+                            int max_examine, float eps, int32_t* nbr, float* dist, int32_t* fb,
+                            unsigned long long* counters, cudaStream_t st) {
+  const int blocks = (int)((nq + 127) / 128);
+  if (K <= 8)
+    k_rerank<D, MC, 8><<<blocks, 128, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
+                                               li, nsplit, K, exact, max_examine, eps, nbr, dist, fb,
+                                               counters);
+  else
+    k_rerank<D, MC, 16><<<blocks, 128, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin,
+                                                ld, li, nsplit, K, exact, max_examine, eps, nbr, dist,
+                                                fb, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
+                          const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
+                          int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
+                          int exact, int max_examine, int32_t* nbr, float* dist, int32_t* fb,
+                          unsigned long long* counters, cudaStream_t st) {
+  const float eps = 1.0f / 65536.0f;
+  if (nsplit > 8) return cudaErrorInvalidValue;
+#define ZOOM_RR(DD, MM)                                                                          \
+  return rerank_k<DD, MM>(K, qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld, li, nsplit, \
+                          exact, max_examine, eps, nbr, dist, fb, counters, st)
+  if (d == 25 && MC == 16) ZOOM_RR(25, 16);
+  if (d == 25 && MC == 32) ZOOM_RR(25, 32);
+  if (d == 9 && MC == 16) ZOOM_RR(9, 16);
+  if (d == 9 && MC == 32) ZOOM_RR(9, 32);
+#undef ZOOM_RR
+  return cudaErrorInvalidValue;
+}

@@ -65,9 +65,11 @@ bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string
     if (!(p->sigma_spatial > 0.f) || !(p->sigma_range > 0.f)) { why = "sigmas must be > 0"; return false; }
   }
   if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return false; }
-  if (p->precision == 1 && (p->rerank_mult < 1 || p->rerank_mult * p->K > 64)) {
-    why = "rerank_mult * K must be in K..64"; return false;
+  if (p->precision == 1 && (p->rerank_mult < 1 || p->rerank_mult * p->K > 32)) {
+    why = "rerank_mult * K must be in K..32"; return false;
   }
+  if (p->search < 0 || p->search > 2) { why = "search must be 0, 1 or 2"; return false; }
+  if (p->precision == 1 && (d->d != 9 && d->d != 25)) { why = "unsupported patch size"; return false; }
   return true;
 }
 
@@ -350,6 +352,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->w = lsh->w;
   ix->t = lsh->min_table_hits;
   ix->cap = lsh->max_candidates;
+  ix->nd_rows = tc_rows_padded(N, false);
   {
     Carver c(nullptr);
     c.take<float>((size_t)L * k * d->d);
@@ -359,6 +362,8 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     c.take<int32_t>((N + 1) * L);
     c.take<int32_t>(N * L);
     c.take<int32_t>(L);
+    c.take<uint16_t>(ix->nd_rows * 80);
+    c.take<uint16_t>(ix->nd_rows * 32);
     ix->bytes = c.off + 256;
   }
   void* mem = zoom_alloc(ctx, ix->bytes, st);
@@ -374,11 +379,17 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->offs = c.take<int32_t>((N + 1) * L);
   ix->ids = c.take<int32_t>(N * L);
   ix->nuniq = c.take<int32_t>(L);
+  ix->dop16 = c.take<uint16_t>(ix->nd_rows * 80);
+  ix->dopbf = c.take<uint16_t>(ix->nd_rows * 32);
   zoom_status rc = ZOOM_OK;
   cudaError_t e = cudaMemcpyAsync(ix->alpha, alpha, (size_t)L * k * d->d * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ix->beta, beta, (size_t)L * k * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = launch_hash(d->feat, d->dpad, d->d, N, ix->alpha, ix->beta, L, k, ix->w, ix->dkeys, st);
+  if (e == cudaSuccess)
+    e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 0, ix->dop16, nullptr, st);
+  if (e == cudaSuccess)
+    e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 1, ix->dopbf, nullptr, st);
   if (e == cudaSuccess) {
     Scratch scr(ctx, st);
     size_t sb = csr_scratch_bytes(N);
@@ -435,6 +446,61 @@ struct QueryBufs {
   int32_t* bucket_sum;
 };
 
+// Neighbour search: SIMT scan, or the tensor-core filter + exact rerank
+// (+ SIMT re-run of the queries the rerank could not settle).
+cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
+                       cudaStream_t st, bool& oom) {
+  zoom_dict d = ix->dict;
+  zoom_ctx ctx = d->ctx;
+  const int K = prm->K;
+  const bool tc = prm->precision == 1 || prm->search == 2 || (prm->search == 0 && d->n >= 4096);
+  if (!tc)
+    return launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, nullptr,
+                            nullptr, st);
+  const int prec = prm->precision;
+  const int MC = tc_list_size(prec, K, prm->rerank_mult);
+  const int64_t nd_tiles = ix->nd_rows / 128;
+  const int64_t nq_pairs = (nq + 255) / 256;
+  const int64_t row_bytes = prec == 0 ? 160 : 64;
+  // splits: each split's operand stays well inside L2 while all CTAs stream
+  // it, and there are enough (query pair, split) items to fill the GPU
+  int64_t s_l2 = (ix->nd_rows * row_bytes + (32ll << 20) - 1) / (32ll << 20);
+  int64_t s_fill = (2ll * ctx->n_sm + nq_pairs - 1) / nq_pairs;
+  int64_t nsplit = std::max<int64_t>(1, std::max(s_l2, s_fill));
+  nsplit = std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles));
+  const int64_t q_rows = tc_rows_padded(nq, true);
+  const int KCH = prec == 0 ? 80 : 32;
+  Carver c(nullptr);
+  c.take<uint16_t>(q_rows * KCH);
+  c.take<float>(nq);
+  c.take<float>(nsplit * nq * MC);
+  c.take<int32_t>(nsplit * nq * MC);
+  c.take<int32_t>(nq);
+  Scratch scr(ctx, st);
+  if (!scr.get(c.off + 256)) {
+    oom = true;
+    return cudaSuccess;
+  }
+  Carver s2(scr.p);
+  uint16_t* qop = s2.take<uint16_t>(q_rows * KCH);
+  float* qn = s2.take<float>(nq);
+  float* ld = s2.take<float>(nsplit * nq * MC);
+  int32_t* li = s2.take<int32_t>(nsplit * nq * MC);
+  int32_t* fb = s2.take<int32_t>(nq);
+  cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, q_rows, 0, prec, qop, qn, st);
+  if (e == cudaSuccess)
+    e = launch_knn_tc(qop, qn, nq, prec == 0 ? ix->dop16 : ix->dopbf, d->n, prec, MC, (int)nsplit,
+                      ctx->n_sm, ld, li, ctx->d_status, st);
+  if (e == cudaSuccess)
+    e = launch_rerank(d->d, MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
+                      ix->t, ld, li, (int)nsplit, prec == 0 ? 1 : 0, prm->rerank_mult * K, b.nbr,
+                      b.dist, fb, ctx->d_counters, st);
+  if (e == cudaSuccess)
+    e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
+                         ctx->d_counters + CNT_FALLBACK, st);
+  return e;
+}
+
 zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
                             const zoom_upscale_params* prm, const QueryBufs& b, cudaStream_t st) {
   zoom_dict d = ix->dict;
@@ -448,8 +514,9 @@ zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
   zoom_stage_mark(ctx, 2, st);
   if (e == cudaSuccess) e = launch_bucket_lookup(ix, b.keys, nq, b.bucket_sum, ctx->d_counters, st);
   zoom_stage_mark(ctx, 3, st);
-  if (e == cudaSuccess)
-    e = launch_knn_exact(ix, b.feat, b.keys, nq, prm->K, b.nbr, b.dist, ctx->d_counters, st);
+  bool oom = false;
+  if (e == cudaSuccess) e = run_search(ix, prm, b, nq, st, oom);
+  if (oom) return fail(ZOOM_ERR_OOM, "neighbour search scratch");
   zoom_stage_mark(ctx, 4, st);
   if (e == cudaSuccess)
     e = launch_lle(d, b.feat, nq, b.nbr, b.dist, prm->K, prm->reg_rel, prm->fp64_cond_threshold,
@@ -484,7 +551,6 @@ zoom_status zoom_query(zoom_index ix, const float* lr, int32_t h, int32_t w,
   zoom_dict d = ix->dict;
   std::string why;
   if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
-  if (prm->precision != 0) return fail(ZOOM_ERR_UNSUPPORTED, "precision 1 not built yet");
   if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
@@ -574,7 +640,6 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   zoom_dict d = ix->dict;
   std::string why;
   if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
-  if (prm->precision != 0) return fail(ZOOM_ERR_UNSUPPORTED, "precision 1 not built yet");
   if (scale != d->s) return fail(ZOOM_ERR_INVALID_ARG, "scale differs from the dictionary's");
   if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
   cudaStream_t st = (cudaStream_t)stream;

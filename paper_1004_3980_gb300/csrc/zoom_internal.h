@@ -65,6 +65,10 @@ struct zoom_index_s {
   int32_t* offs = nullptr;   // [L][N+1] CSR offsets into ids
   int32_t* ids = nullptr;    // [L][N]   entry IDs grouped by bin, ascending within a bin
   int32_t* nuniq = nullptr;  // [L]
+  // tensor-core operands of the dictionary: 128-row tiles [tile][kc][128][8]
+  uint16_t* dop16 = nullptr; // FP16 3-term split, 10 chunks of 8 per row
+  uint16_t* dopbf = nullptr; // BF16 single term, 4 chunks of 8 per row
+  int64_t nd_rows = 0;       // rows of the operands (N rounded up to 128)
   size_t bytes = 0;
 };
 
@@ -100,10 +104,26 @@ cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t n
                                  cudaStream_t st);
 cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
                              int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                             const int32_t* qidx, const unsigned long long* qcount,
                              cudaStream_t st);
 cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
                        const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
                        unsigned long long* counters, cudaStream_t st);
+
+// tensor-core neighbour search (kernels_tc.cu)
+int64_t tc_rows_padded(int64_t n, bool even_tiles);
+cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
+                           int precision, uint16_t* op, float* norm_out, cudaStream_t st);
+size_t tc_smem_bytes(int precision);
+int tc_list_size(int precision, int K, int rerank_mult);
+cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
+                          int64_t nd, int precision, int MC, int nsplit, int grid, float* out_d,
+                          int32_t* out_id, unsigned int* status, cudaStream_t st);
+cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
+                          const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
+                          int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
+                          int exact, int max_examine, int32_t* nbr, float* dist, int32_t* fb,
+                          unsigned long long* counters, cudaStream_t st);
 
 // image steps (kernels_image.cu)
 cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float* mu,

@@ -63,11 +63,12 @@ class UpscaleParams:
     precision: int = 0
     rerank_mult: int = 4
     fp64_cond_threshold: float = 1e6
+    search: int = 0
 
     def c(self) -> capi.UpscaleParams:
         return capi.UpscaleParams(self.K, self.reg_rel, self.bp_iters, self.sigma_spatial,
                                   self.sigma_range, self.bp_radius, self.precision,
-                                  self.rerank_mult, self.fp64_cond_threshold)
+                                  self.rerank_mult, self.fp64_cond_threshold, self.search)
 
 
 class Context:
