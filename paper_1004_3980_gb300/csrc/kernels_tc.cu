@@ -205,6 +205,21 @@ __device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float 
   thr = ld[MC - 1];
 }
 
+// v[j] for a run-time j in [0, 32) by a binary tree of selects, keeping v in
+// registers.
+__device__ __forceinline__ float select32(const float (&v)[32], int j) {
+  float a[16], b[8], c[4], d[2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) b[i] = (j & 8) ? a[i + 8] : a[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? b[i + 4] : b[i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) d[i] = (j & 2) ? c[i + 2] : c[i];
+  return (j & 1) ? d[1] : d[0];
+}
+
 template <int KC, int MC, uint32_t AB_TYPE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
@@ -372,10 +387,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
 #pragma unroll
           for (int j = 1; j < 32; ++j) m = fminf(m, v[j]);
           if (m < thr) {
-            const int col0 = t * TC_ROWS + c * 32;
+            // rare: collect the columns below the threshold, then insert
+            // only those (one select tree per hit, no local memory)
+            uint32_t mask = 0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (v[j] < thr) list_push<MC>(ld, li, v[j], col0 + j, thr);
+            for (int j = 0; j < 32; ++j) mask |= (v[j] < thr ? 1u : 0u) << j;
+            const int col0 = t * TC_ROWS + c * 32;
+            while (mask) {
+              const int j = __ffs(mask) - 1;
+              mask &= mask - 1;
+              const float val = select32(v, j);
+              if (val < thr) list_push<MC>(ld, li, val, col0 + j, thr);
+            }
           }
         }
         tc_fence_before();

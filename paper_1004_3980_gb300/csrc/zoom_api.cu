@@ -464,7 +464,7 @@ cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const Quer
   const int64_t row_bytes = prec == 0 ? 160 : 64;
   // splits: each split's operand stays well inside L2 while all CTAs stream
   // it, and there are enough (query pair, split) items to fill the GPU
-  int64_t s_l2 = (ix->nd_rows * row_bytes + (32ll << 20) - 1) / (32ll << 20);
+  int64_t s_l2 = (ix->nd_rows * row_bytes + (64ll << 20) - 1) / (64ll << 20);
   int64_t s_fill = (2ll * ctx->n_sm + nq_pairs - 1) / nq_pairs;
   int64_t nsplit = std::max<int64_t>(1, std::max(s_l2, s_fill));
   nsplit = std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles));
