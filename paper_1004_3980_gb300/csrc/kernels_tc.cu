@@ -28,7 +28,10 @@
 namespace {
 
 constexpr int TC_THREADS = 320;   // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
-constexpr int TC_STAGES = 4;
+// Dictionary-tile ring depth: enough bulk copies in flight to cover their
+// latency, within the shared memory left by the query tiles and the buffers.
+__host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 5 : 16; }
+constexpr int kBarBytes = 512;
 constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
 constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
 
@@ -65,6 +68,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// As mbar_try_wait, but the thread may sleep in hardware until the phase
+// completes or about `hint_ns` pass, instead of re-issuing polls.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 
 // Waits for the phase of `parity` to complete.  Gives up after kWaitNs (or
 // 2^30 polls), or as soon as another role gave up: then it raises the shared
@@ -74,11 +90,9 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 0; it < (1u << 30); ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > kWaitNs) break;
-    }
+    if (mbar_try_wait_sleep(bar, parity, 1000000u)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitNs) break;
   }
   *abort_flag = 1;
   atomicExch(status, 1u);
@@ -126,6 +140,26 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
+}
+
+// Issues the load of 32 consecutive TMEM columns of this warp's 32 lanes
+// (one lane per thread); the registers are valid after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // 32 consecutive TMEM columns of this warp's 32 lanes (one lane per thread).
@@ -205,22 +239,65 @@ __device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float 
   thr = ld[MC - 1];
 }
 
-// v[j] for a run-time j in [0, 32) by a binary tree of selects, keeping v in
-// registers.
-__device__ __forceinline__ float select32(const float (&v)[32], int j) {
-  float a[16], b[8], c[4], d[2];
+// Per epilogue lane, columns below the threshold are first appended to a
+// shared-memory buffer of kBuf slots (a few instructions per column) and
+// merged into the sorted register list when some lane of the warp runs out
+// of room: the merge loop then runs for all lanes together, so the sorted
+// insertions execute with the warp converged.
+constexpr int kBuf = 40;
+
+template <int MC>
+__device__ __forceinline__ void flush_appends(float (&ld)[MC], int (&li)[MC], float& thr,
+                                              const float* bv, const int* bi, int& cnt) {
+  const int n = cnt;
+  const int nmax = __reduce_max_sync(0xffffffffu, n);
+  for (int s = 0; s < nmax; ++s) {
+    if (s < n) {
+      const float x = bv[s * 256];
+      if (x < thr) list_push<MC>(ld, li, x, bi[s * 256], thr);
+    }
+  }
+  cnt = 0;
+}
+
+// One 32-column chunk of a query's accumulator row: the chunk minimum is
+// compared with the list threshold; columns below it are appended.
+template <int MC>
+__device__ __forceinline__ void scan_chunk(const float (&v)[32], int col0, float (&ld)[MC], int (&li)[MC],
+                                           float& thr, float* bv, int* bi, int& cnt) {
+  // room for the up to 32 appends of this chunk in every lane
+  if (__any_sync(0xffffffffu, cnt > kBuf - 32)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+  float gm[4];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = (j & 16) ? v[i + 16] : v[i];
+  for (int g = 0; g < 4; ++g) {
+    gm[g] = v[g * 8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) b[i] = (j & 8) ? a[i + 8] : a[i];
+    for (int j = 1; j < 8; ++j) gm[g] = fminf(gm[g], v[g * 8 + j]);
+  }
+  const float m = fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3]));
+  if (m < thr) {
+    // rare: append the columns below the (possibly stale) threshold to this
+    // lane's buffer; they are merged into the list later, by the whole warp
 #pragma unroll
-  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? b[i + 4] : b[i];
+    for (int g = 0; g < 4; ++g) {
+      if (gm[g] < thr) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i) d[i] = (j & 2) ? c[i + 2] : c[i];
-  return (j & 1) ? d[1] : d[0];
+        for (int j = 0; j < 8; ++j) {
+          const float x = v[g * 8 + j];
+          if (x < thr) {
+            bv[cnt * 256] = x;
+            bi[cnt * 256] = col0 + g * 8 + j;
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
 }
 
 template <int KC, int MC, uint32_t AB_TYPE>
+// Ten warps sit 3/3/2/2 on the four SM sub-partitions (16K registers each),
+// which caps a thread at 168 registers.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
   constexpr int kKSteps = KC / 2;                     // MMA K = 16 = two 8-element chunks
@@ -228,22 +305,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;                                  // 2 query tiles
-  unsigned char* sB = smem + 2 * kTileBytes;                 // TC_STAGES dictionary tiles
-  uint64_t* bars = (uint64_t*)(sB + TC_STAGES * kTileBytes);
+  constexpr int kStages = tc_stages(KC);
+  unsigned char* sB = smem + 2 * kTileBytes;                 // kStages dictionary tiles
+  uint64_t* bars = (uint64_t*)(sB + kStages * kTileBytes);
   uint64_t* a_full = bars + 0;
   uint64_t* a_empty = bars + 1;
-  uint64_t* b_full = bars + 2;                 // [TC_STAGES]
-  uint64_t* b_empty = b_full + TC_STAGES;      // [TC_STAGES]
-  uint64_t* acc_full = b_empty + TC_STAGES;    // [2]
+  uint64_t* b_full = bars + 2;                 // [kStages]
+  uint64_t* b_empty = b_full + kStages;        // [kStages]
+  uint64_t* acc_full = b_empty + kStages;      // [2]
   uint64_t* acc_empty = acc_full + 2;          // [2]
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBuf][256]
+  int* buf_i = (int*)(buf_v + kBuf * 256);               // [kBuf][256]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
     mbar_init(a_empty, 1);
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(b_full + s, 1);
       mbar_init(b_empty + s, 1);
     }
@@ -287,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
           mbar_arrive_expect_tx(b_full + stage, kTileBytes);
           bulk_g2s(sB + stage * kTileBytes, (const unsigned char*)a.dop + (size_t)t * kTileBytes,
                    kTileBytes, b_full + stage);
-          if (++stage == TC_STAGES) {
+          if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
@@ -331,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
           mma_commit(acc_full + buf);
           accp[buf] ^= 1u;
           buf ^= 1;
-          if (++stage == TC_STAGES) {
+          if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
@@ -350,6 +430,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
     const int qt = ew >> 2;             // query tile within the pair
     const int quad = warp & 3;          // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;   // row in the 128-row tile
+    // this lane's append buffer: slot s at [s * 256] (one bank per lane)
+    float* bv = buf_v + ew * 32 + lane;
+    int* bi = buf_i + ew * 32 + lane;
     int buf = 0;
     uint32_t accp[2] = {0u, 0u};
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -368,6 +451,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         li[j] = -1;
       }
       float thr = FLT_MAX;   // in acc units: d~ - ||q||^2
+      int cnt = 0;           // entries in this lane's append buffer
       bool ok = true;
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
@@ -379,26 +463,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         }
         tc_fence_after();
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
+        if constexpr (MC <= 16) {
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-          float v[32];
-          tmem_ld32(tb + c * 32, v);
-          float m = v[0];
-#pragma unroll
-          for (int j = 1; j < 32; ++j) m = fminf(m, v[j]);
-          if (m < thr) {
-            // rare: collect the columns below the threshold, then insert
-            // only those (one select tree per hit, no local memory)
-            uint32_t mask = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) mask |= (v[j] < thr ? 1u : 0u) << j;
-            const int col0 = t * TC_ROWS + c * 32;
-            while (mask) {
-              const int j = __ffs(mask) - 1;
-              mask &= mask - 1;
-              const float val = select32(v, j);
-              if (val < thr) list_push<MC>(ld, li, val, col0 + j, thr);
-            }
+          for (int h = 0; h < 2; ++h) {
+            // two 32-column loads in flight per wait
+            float va[32], vb[32];
+            tmem_ld32_issue(tb + h * 64, va);
+            tmem_ld32_issue(tb + h * 64 + 32, vb);
+            tmem_ld_wait();
+            scan_chunk<MC>(va, t * TC_ROWS + h * 64, ld, li, thr, bv, bi, cnt);
+            scan_chunk<MC>(vb, t * TC_ROWS + h * 64 + 32, ld, li, thr, bv, bi, cnt);
+          }
+        } else {
+          // the longer list leaves registers for one chunk at a time
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c) {
+            float v[32];
+            tmem_ld32_issue(tb + c * 32, v);
+            tmem_ld_wait();
+            scan_chunk<MC>(v, t * TC_ROWS + c * 32, ld, li, thr, bv, bi, cnt);
           }
         }
         tc_fence_before();
@@ -407,6 +490,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         buf ^= 1;
       }
       if (!ok) break;
+      flush_appends<MC>(ld, li, thr, bv, bi, cnt);
       if (valid) {
         float* od = a.out_d + ((int64_t)split * a.nq + q) * MC;
         int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
@@ -706,10 +790,8 @@ cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_
 
 size_t tc_smem_bytes(int precision) {
   const int KC = precision == 0 ? 10 : 4;
-  // alignment pad + operand tiles + barriers, plus 64 KB of slack so that
-  // every address a descriptor of these tiles can form stays inside the
-  // allocation (one CTA per SM either way)
-  return 1024 + (size_t)(2 + TC_STAGES) * KC * TC_ROWS * 16 + 256 + 64 * 1024;
+  // alignment pad + operand tiles + barriers + the epilogue append buffers
+  return 1024 + (size_t)(2 + tc_stages(KC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)kBuf * 256 * 8;
 }
 
 int tc_list_size(int precision, int K, int rerank_mult) {

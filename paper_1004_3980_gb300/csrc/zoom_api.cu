@@ -461,13 +461,13 @@ cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const Quer
   const int MC = tc_list_size(prec, K, prm->rerank_mult);
   const int64_t nd_tiles = ix->nd_rows / 128;
   const int64_t nq_pairs = (nq + 255) / 256;
-  const int64_t row_bytes = prec == 0 ? 160 : 64;
-  // splits: each split's operand stays well inside L2 while all CTAs stream
-  // it, and there are enough (query pair, split) items to fill the GPU
-  int64_t s_l2 = (ix->nd_rows * row_bytes + (64ll << 20) - 1) / (64ll << 20);
-  int64_t s_fill = (2ll * ctx->n_sm + nq_pairs - 1) / nq_pairs;
-  int64_t nsplit = std::max<int64_t>(1, std::max(s_l2, s_fill));
-  nsplit = std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles));
+  // Every CTA streams the dictionary tiles in the same order at about the
+  // same pace, so L2 serves nearly all of them whatever the dictionary size.
+  // A split restarts every query's best list (about MC*ln(N/MC) insertions
+  // each), so the dictionary is split only as far as needed to give every SM
+  // (query pair, split) items.
+  int64_t nsplit = (2ll * ctx->n_sm + nq_pairs - 1) / nq_pairs;
+  nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
   const int64_t q_rows = tc_rows_padded(nq, true);
   const int KCH = prec == 0 ? 80 : 32;
   Carver c(nullptr);
