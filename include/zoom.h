@@ -208,6 +208,28 @@ zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt
 zoom_status zoom_backproject(zoom_ctx ctx, const zoom_degradation* degr, const float* lr, int32_t h,
                              int32_t w, const zoom_upscale_params* prm, float* hr, void* stream);
 
+/* zoom_backproject_noalloc: zoom_backproject for callers that cannot
+ * allocate device memory (for instance code living inside another
+ * framework's fixed memory budget, real-time pipelines whose memory is
+ * reserved up front, or work being recorded where an allocation would break
+ * the recording).  The paper has no counterpart: this is a service of this
+ * library.  It takes a CUDA device index instead of a context (creating a
+ * context allocates) and makes that device current.  Inputs and outputs are
+ * as for zoom_backproject; it calls no allocator.  Its scratch memory (the
+ * second HR image and the LR error image) is a library-owned static device
+ * array of ZOOM_NOALLOC_SCRATCH_FLOATS floats (8 MiB), held by every GPU
+ * that loads the library until the process exits; an image needs
+ * round_up((s*h)*(s*w), 64) + h*w floats of it, larger requests return
+ * ZOOM_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress): make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps
+ * on the GPU (different streams, or threads without ordering) race; order
+ * them on one stream. */
+#define ZOOM_NOALLOC_SCRATCH_FLOATS (2u * 1024u * 1024u)
+zoom_status zoom_backproject_noalloc(int device, const zoom_degradation* degr, const float* lr,
+                                     int32_t h, int32_t w, const zoom_upscale_params* prm,
+                                     float* hr, void* stream);
+
 /* zoom_get_stats: synchronises `stream` and returns the counters of the
  * last zoom_query / zoom_upscale on ctx. */
 zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out);

@@ -28,6 +28,7 @@ SOURCES = [
     "kernels_query.cu",
     "kernels_image.cu",
     "kernels_tc.cu",
+    "zoom_noalloc.cu",
 ]
 HEADERS = ["zoom_internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
