@@ -208,6 +208,53 @@ zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt
 zoom_status zoom_backproject(zoom_ctx ctx, const zoom_degradation* degr, const float* lr, int32_t h,
                              int32_t w, const zoom_upscale_params* prm, float* hr, void* stream);
 
+/* ---- differentiation (Sec. 4: posterior Eq. 5, likelihood Eq. 8, prior
+ * Eq. 9; back-projection Eq. 6-7 as a MAP gradient step) ------------------ */
+
+/* zoom_degrade: lr = D_s(B hr) (Sec. 2.1) in FP32; hr device H x W, lr
+ * device (H/s) x (W/s) (sizes not divisible by s are cropped). */
+zoom_status zoom_degrade(zoom_ctx ctx, const zoom_degradation* degr, const float* hr, int32_t H,
+                         int32_t W, float* lr, void* stream);
+
+/* zoom_degrade_adjoint: g_hr = B^T D^T g_lr, the adjoint of zoom_degrade for
+ * H = s*h, W = s*w; g_lr device h x w, g_hr device (s*h) x (s*w). */
+zoom_status zoom_degrade_adjoint(zoom_ctx ctx, const zoom_degradation* degr, const float* g_lr,
+                                 int32_t h, int32_t w, float* g_hr, void* stream);
+
+/* zoom_reconstruct_with: zoom_reconstruct (Eq. 14 + overlap average) with a
+ * caller-supplied HR dictionary hr_res (device [N][hr_stride] floats, row n
+ * = the HR patch of ID n minus its LR mean, row-major (s*P)^2 values,
+ * hr_stride >= (s*P)^2). */
+zoom_status zoom_reconstruct_with(zoom_index ix, const float* hr_res, int32_t hr_stride,
+                                  const int32_t* nbr, const float* wgt, const float* mu, int32_t h,
+                                  int32_t w, int32_t K, float* hr, void* stream);
+
+/* zoom_reconstruct_adjoint: the adjoint of the reconstruction with the
+ * neighbours and weights fixed.  Given grad_hr = dL/d(HR image) (device
+ * (s*h) x (s*w)), writes grad_dict = dL/dR (device [N][grad_stride], every
+ * row; rows of unused entries are 0) and, if grad_mu != NULL, dL/dmu (device
+ * [n_q]).  The sum over the uses of an entry runs in ascending use order
+ * (deterministic; no atomics).  grad_dict may be NULL. */
+zoom_status zoom_reconstruct_adjoint(zoom_index ix, const int32_t* nbr, const float* wgt, int32_t h,
+                                     int32_t w, int32_t K, const float* grad_hr, float* grad_dict,
+                                     int32_t grad_stride, float* grad_mu, void* stream);
+
+/* zoom_backward: the MAP energy of an LR image lr (device h x w) with fixed
+ * neighbours nbr (device [n_q][K]),
+ *   E(R) = || D B x - y ||^2 + lambda * sum over 4-neighbour patch pairs of
+ *          the squared difference of their HR patches on the overlap,
+ *   x = overlap average of P_n = mu_n + sum_m w_nm R[nbr_nm],
+ * and its gradients.  wgt (device [n_q][K]) gives the LLE weights; NULL
+ * recomputes them from the LR features (Eq. 12-13, regulariser reg_rel).
+ * Outputs (any may be NULL): grad_x = 2 B^T D^T (D B x - y) (device HR: the
+ * gradient of the data term at x, i.e. the MAP back-projection direction),
+ * grad_dict = dE/dR (device [N][grad_stride]), hr_out = x (device HR),
+ * energy (host; when given, the call synchronises `stream`). */
+zoom_status zoom_backward(zoom_index ix, const float* lr, int32_t h, int32_t w, const int32_t* nbr,
+                          const float* wgt, int32_t K, float reg_rel, float lambda, float* grad_x,
+                          float* grad_dict, int32_t grad_stride, float* hr_out, double* energy,
+                          void* stream);
+
 /* zoom_backproject_noalloc: zoom_backproject for callers that cannot
  * allocate device memory (for instance code living inside another
  * framework's fixed memory budget, real-time pipelines whose memory is

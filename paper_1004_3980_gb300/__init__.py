@@ -6,5 +6,7 @@ average, cross-bilateral error back-projection.
 The compute path is libzoom.so (hand-written CUDA behind the C ABI of
 include/zoom.h); this package only marshals arguments.
 """
-from .zoom import (Context, Dictionary, Index, UpscaleParams, backproject, query,  # noqa: F401
-                   reconstruct, upscale)
+from .zoom import (Context, DegradeFunction, Dictionary, Index, ReconstructFunction,  # noqa: F401
+                   UpscaleParams, backproject, degrade, degrade_adjoint, dictionary_hr,
+                   map_energy_grads, query, reconstruct, reconstruct_adjoint, reconstruct_with,
+                   upscale)

@@ -29,6 +29,8 @@ SOURCES = [
     "kernels_image.cu",
     "kernels_tc.cu",
     "zoom_noalloc.cu",
+    "kernels_backward.cu",
+    "zoom_api_backward.cu",
 ]
 HEADERS = ["zoom_internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

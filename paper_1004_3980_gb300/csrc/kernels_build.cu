@@ -371,6 +371,53 @@ cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const flo
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_make_pairs(const int32_t* __restrict__ keys32, int64_t n, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ vals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = (uint64_t)(uint32_t)keys32[i];
+  vals[i] = (int32_t)i;
+}
+}  // namespace
+
+// Stable sort of the positions 0..n-1 by a non-negative int32 key, then the
+// CSR of equal-key runs: sorted_pos[n] (positions grouped by key, ascending
+// within a run), ukeys[u] (run keys, ascending), offs[u+1], *nuniq = u.
+cudaError_t sort_keys_csr(const int32_t* keys32, int64_t n, int32_t* sorted_pos, uint64_t* ukeys,
+                          int32_t* offs, int32_t* nuniq, void* scratch, size_t scratch_bytes,
+                          cudaStream_t st) {
+  if (scratch_bytes < csr_scratch_bytes(n)) return cudaErrorInvalidValue;
+  const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+  char* p = (char*)scratch;
+  uint64_t* ka = (uint64_t*)p; p += n * 8;
+  uint64_t* kb = (uint64_t*)p; p += n * 8;
+  int32_t* va = (int32_t*)p; p += n * 4;
+  int32_t* vb = (int32_t*)p; p += n * 4;
+  int32_t* hist = (int32_t*)p; p += (int64_t)256 * ntiles * 4;
+  int32_t* head = (int32_t*)p; p += n * 4;
+  int32_t* pos = (int32_t*)p; p += n * 4;
+  int32_t* part = (int32_t*)p;
+  const int eb = (int)((n + 255) / 256);
+  k_make_pairs<<<eb, 256, 0, st>>>(keys32, n, ka, va);
+  uint64_t* kin = ka; uint64_t* kout = kb;
+  int32_t* vin = va; int32_t* vout = vb;
+  for (int shift = 0; shift < 32; shift += 8) {   // keys fit in 32 bits
+    k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+    cudaError_t e = exclusive_scan(hist, hist, (int64_t)256 * ntiles, part, st);
+    if (e != cudaSuccess) return e;
+    k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  k_csr_heads<<<eb, 256, 0, st>>>(kin, n, head);
+  cudaError_t e = exclusive_scan(head, pos, n, part, st);
+  if (e != cudaSuccess) return e;
+  k_csr_write<<<eb, 256, 0, st>>>(kin, head, pos, n, ukeys, offs, nuniq);
+  cudaMemcpyAsync(sorted_pos, vin, n * 4, cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError();
+}
+
 size_t csr_scratch_bytes(int64_t n) {
   int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
   int64_t hist = 256 * ntiles;

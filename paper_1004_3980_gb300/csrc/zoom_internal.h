@@ -125,6 +125,27 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
                           int exact, int max_examine, int32_t* nbr, float* dist, int32_t* fb,
                           unsigned long long* counters, cudaStream_t st);
 
+// backward / adjoint steps (kernels_backward.cu) and the key sort (kernels_build.cu)
+cudaError_t sort_keys_csr(const int32_t* keys32, int64_t n, int32_t* sorted_pos, uint64_t* ukeys,
+                          int32_t* offs, int32_t* nuniq, void* scratch, size_t scratch_bytes,
+                          cudaStream_t st);
+cudaError_t launch_patches(const int32_t* nbr, const float* wgt, const float* mu, const float* hr_res,
+                           int ph2pad, int K, int64_t nq, int ph2, float* P, cudaStream_t st);
+cudaError_t launch_degrade(const float* x, int H, int W, int s, double sigma, const float* sub, float* y,
+                           cudaStream_t st);
+cudaError_t launch_degrade_adjoint(const float* r, int h, int w, int H, int W, int s, double sigma,
+                                   float alpha, float* g, cudaStream_t st);
+cudaError_t launch_patch_grad(const float* gx, const float* P, int h, int w, int s, int Pp, float lambda,
+                              float* gP, cudaStream_t st);
+cudaError_t launch_dict_grad(const int32_t* sorted_use, const int32_t* offs, const uint64_t* ukeys,
+                             const int32_t* nuniq, int64_t max_segments, const float* wgt, const float* gP,
+                             int K, int ph2, int ph2pad_out, float* grad, cudaStream_t st);
+cudaError_t launch_mu_grad(const float* gP, int64_t nq, int ph2, float* gmu, cudaStream_t st);
+cudaError_t launch_energy_partials(const float* r, int64_t n_r, const float* P, int h, int w, int s, int Pp,
+                                   double* part, int nblocks, cudaStream_t st);
+cudaError_t launch_nbr_dist(const float* qfeat, int dpad, int d, int64_t nq, const float* dfeat,
+                            const int32_t* nbr, int K, float* dist, cudaStream_t st);
+
 // image steps (kernels_image.cu)
 cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float* mu,
                                const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,

@@ -270,3 +270,112 @@ def backproject(ctx: Context, lr: torch.Tensor, hr: torch.Tensor, scale: int,
     capi.call("zoom_backproject", ctx.handle, C.byref(degr), _ptr(lr), h, w, C.byref(cp), _ptr(hr),
               _stream(stream))
     return hr
+
+
+# ---------------------------------------------------------------------------
+# differentiation
+# ---------------------------------------------------------------------------
+
+
+def dictionary_hr(dictionary: Dictionary, stream=None) -> torch.Tensor:
+    """The HR residual patches R of a dictionary as a CUDA tensor [N][(s*P)^2]."""
+    _, _, hr = dictionary.export(stream)
+    return torch.from_numpy(hr).cuda(dictionary.ctx.device)
+
+
+def degrade(ctx: Context, hr: torch.Tensor, scale: int, blur_sigma: float = 0.8, stream=None) -> torch.Tensor:
+    """lr = D_s(B hr) (blur + s x s box down-sampling) on the GPU."""
+    _need(hr, torch.float32, "hr")
+    H, W = hr.shape
+    out = torch.empty((H // scale, W // scale), dtype=torch.float32, device=hr.device)
+    degr = capi.Degradation(scale, 1, blur_sigma)
+    capi.call("zoom_degrade", ctx.handle, C.byref(degr), _ptr(hr), H, W, _ptr(out), _stream(stream))
+    return out
+
+
+def degrade_adjoint(ctx: Context, g_lr: torch.Tensor, scale: int, blur_sigma: float = 0.8,
+                    stream=None) -> torch.Tensor:
+    """B^T D^T g_lr, the adjoint of `degrade`."""
+    _need(g_lr, torch.float32, "g_lr")
+    h, w = g_lr.shape
+    out = torch.empty((scale * h, scale * w), dtype=torch.float32, device=g_lr.device)
+    degr = capi.Degradation(scale, 1, blur_sigma)
+    capi.call("zoom_degrade_adjoint", ctx.handle, C.byref(degr), _ptr(g_lr), h, w, _ptr(out), _stream(stream))
+    return out
+
+
+def reconstruct_with(index: Index, hr_dict: torch.Tensor, nbr, wgt, mu, h: int, w: int,
+                     stream=None) -> torch.Tensor:
+    """Eq. 14 blend + overlap average with a given HR dictionary [N][(s*P)^2]."""
+    for t, dt, nm in ((hr_dict, torch.float32, "hr_dict"), (nbr, torch.int32, "nbr"),
+                      (wgt, torch.float32, "wgt"), (mu, torch.float32, "mu")):
+        _need(t, dt, nm)
+    s = index.dictionary.scale
+    out = torch.empty((s * h, s * w), dtype=torch.float32, device=nbr.device)
+    capi.call("zoom_reconstruct_with", index.handle, _ptr(hr_dict), hr_dict.shape[1], _ptr(nbr), _ptr(wgt),
+              _ptr(mu), h, w, nbr.shape[1], _ptr(out), _stream(stream))
+    return out
+
+
+def reconstruct_adjoint(index: Index, nbr, wgt, h: int, w: int, grad_hr: torch.Tensor,
+                        want_mu: bool = False, stream=None):
+    """dL/dR (and optionally dL/dmu) from dL/d(HR image), neighbours fixed."""
+    _need(grad_hr, torch.float32, "grad_hr")
+    d = index.dictionary
+    ph2 = (d.scale * d.patch) ** 2
+    gd = torch.empty((d.n, ph2), dtype=torch.float32, device=nbr.device)
+    gmu = torch.empty(nbr.shape[0], dtype=torch.float32, device=nbr.device) if want_mu else None
+    capi.call("zoom_reconstruct_adjoint", index.handle, _ptr(nbr), _ptr(wgt), h, w, nbr.shape[1],
+              _ptr(grad_hr), _ptr(gd), ph2, _ptr(gmu), _stream(stream))
+    return gd, gmu
+
+
+class ReconstructFunction(torch.autograd.Function):
+    """x = overlap average of mu_n + sum_m w_nm R[nbr_nm] as a differentiable
+    function of the HR dictionary R (neighbours and weights fixed); the
+    backward is the library's adjoint kernel."""
+
+    @staticmethod
+    def forward(fctx, hr_dict, index, nbr, wgt, mu, h, w):
+        fctx.save_for_backward(nbr, wgt)
+        fctx.index, fctx.hw = index, (h, w)
+        return reconstruct_with(index, hr_dict.contiguous(), nbr, wgt, mu, h, w)
+
+    @staticmethod
+    def backward(fctx, g):
+        nbr, wgt = fctx.saved_tensors
+        gd, _ = reconstruct_adjoint(fctx.index, nbr, wgt, *fctx.hw, g.contiguous())
+        return gd, None, None, None, None, None, None
+
+
+class DegradeFunction(torch.autograd.Function):
+    """lr = D_s(B x) as a differentiable function of x; backward B^T D^T."""
+
+    @staticmethod
+    def forward(fctx, x, ctx, scale, blur_sigma):
+        fctx.ctx, fctx.scale, fctx.sigma = ctx, scale, blur_sigma
+        return degrade(ctx, x.contiguous(), scale, blur_sigma)
+
+    @staticmethod
+    def backward(fctx, g):
+        return degrade_adjoint(fctx.ctx, g.contiguous(), fctx.scale, fctx.sigma), None, None, None
+
+
+def map_energy_grads(index: Index, lr: torch.Tensor, nbr: torch.Tensor, wgt: torch.Tensor | None = None,
+                     lam: float = 0.1, reg_rel: float = 1e-3, stream=None) -> dict:
+    """MAP energy E(R) = ||D B x - y||^2 + lam * overlap prior and its
+    gradients dE/dx (data term at x) and dE/dR, neighbours fixed (zoom_backward)."""
+    _need(lr, torch.float32, "lr")
+    _need(nbr, torch.int32, "nbr")
+    if wgt is not None:
+        _need(wgt, torch.float32, "wgt")
+    d = index.dictionary
+    h, w = lr.shape
+    s, ph2 = d.scale, (d.scale * d.patch) ** 2
+    gx = torch.empty((s * h, s * w), dtype=torch.float32, device=lr.device)
+    gd = torch.empty((d.n, ph2), dtype=torch.float32, device=lr.device)
+    x = torch.empty((s * h, s * w), dtype=torch.float32, device=lr.device)
+    e = C.c_double()
+    capi.call("zoom_backward", index.handle, _ptr(lr), h, w, _ptr(nbr), _ptr(wgt), nbr.shape[1], reg_rel, lam,
+              _ptr(gx), _ptr(gd), ph2, _ptr(x), C.byref(e), _stream(stream))
+    return {"energy": e.value, "grad_x": gx, "grad_dict": gd, "hr": x}
