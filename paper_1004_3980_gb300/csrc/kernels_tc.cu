@@ -295,6 +295,92 @@ __device__ __forceinline__ void scan_chunk(const float (&v)[32], int col0, float
   }
 }
 
+// Warp-cooperative best lists (used for the longer lists, MC = 32).  Each
+// epilogue lane owns one query; the list of that query's MC smallest values
+// (ascending) lives in shared memory and is held one entry per lane while
+// the warp works on it.  A column below a query's threshold is inserted by
+// the whole warp at once: a ballot gives its rank, a lane shift makes room.
+constexpr unsigned kFull = 0xffffffffu;
+
+// w[j] for a run-time j in [0, 8) by a binary tree of selects (registers).
+__device__ __forceinline__ float select8(const float (&w)[8], int j) {
+  float c[4], d[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? w[i + 4] : w[i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) d[i] = (j & 2) ? c[i + 2] : c[i];
+  return (j & 1) ? d[1] : d[0];
+}
+
+template <int MC>
+__device__ __forceinline__ void coop_insert(float& e, int& ei, float x, int id, int lane) {
+  // e (lane j) = entry j of the list; lanes >= MC hold FLT_MAX
+  const int pos = __popc(__ballot_sync(kFull, e <= x));   // entries not above x
+  const float eu = __shfl_up_sync(kFull, e, 1);
+  const int iu = __shfl_up_sync(kFull, ei, 1);
+  if (lane > pos) {
+    e = eu;
+    ei = iu;
+  } else if (lane == pos) {
+    e = x;
+    ei = id;
+  }
+  if (lane >= MC) e = FLT_MAX;
+}
+
+// One 32-column chunk of the warp's 32 query rows (lane L holds row L's
+// values v[0..31]): for each lane whose chunk minimum is below its
+// threshold, the warp visits that lane's groups of 8 columns holding values
+// below the threshold and inserts them.
+template <int MC>
+__device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], int col0, float* rows_d, int* rows_i,
+                                                float& thr, int lane) {
+  float gm[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    gm[g] = v[g * 8];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) gm[g] = fminf(gm[g], v[g * 8 + j]);
+  }
+  const float m = fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3]));
+  unsigned hit = __ballot_sync(kFull, m < thr);
+  while (hit) {                                 // warp-uniform from here on
+    const int L = __ffs(hit) - 1;
+    hit &= hit - 1;
+    float tL = __shfl_sync(kFull, thr, L);
+    float* rd = rows_d + L * MC;
+    int* ri = rows_i + L * MC;
+    float e = lane < MC ? rd[lane] : FLT_MAX;
+    int ei = lane < MC ? ri[lane] : -1;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (__shfl_sync(kFull, gm[g], L) < tL) {
+        float w8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w8[j] = v[g * 8 + j];
+        uint32_t msk = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) msk |= (w8[j] < tL ? 1u : 0u) << j;
+        msk = __shfl_sync(kFull, msk, L);      // lane L's columns below its threshold
+        while (msk) {
+          const int j = __ffs(msk) - 1;
+          msk &= msk - 1;
+          const float x = __shfl_sync(kFull, select8(w8, j), L);
+          if (x < tL) {
+            coop_insert<MC>(e, ei, x, col0 + g * 8 + j, lane);
+            tL = __shfl_sync(kFull, e, MC - 1);
+          }
+        }
+      }
+    }
+    if (lane < MC) {
+      rd[lane] = e;
+      ri[lane] = ei;
+    }
+    if (lane == L) thr = tL;
+  }
+}
+
 template <int KC, int MC, uint32_t AB_TYPE>
 // Ten warps sit 3/3/2/2 on the four SM sub-partitions (16K registers each),
 // which caps a thread at 168 registers.
@@ -435,6 +521,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
     int* bi = buf_i + ew * 32 + lane;
     int buf = 0;
     uint32_t accp[2] = {0u, 0u};
+    if constexpr (MC > 16) {
+      // cooperative lists: this warp's 32 lists [32][MC] in the buffer region
+      float* rows_d = buf_v + ew * 32 * MC;
+      int* rows_i = (int*)(buf_v + 256 * MC) + ew * 32 * MC;
+      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
+        const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
+        const int t0 = split * a.tiles_per_split;
+        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+        const int64_t q0 = ((int64_t)qp * 2 + qt) * TC_ROWS + quad * 32;   // lane 0's query
+        const float qn = q0 + lane < a.nq ? a.qn[q0 + lane] : 0.f;
+        for (int L = 0; L < 32; ++L)
+          if (lane < MC) {
+            rows_d[L * MC + lane] = FLT_MAX;
+            rows_i[L * MC + lane] = -1;
+          }
+        __syncwarp();
+        float thr = FLT_MAX;
+        bool ok = true;
+        for (int t = t0; t < t1; ++t) {
+          const bool w = __all_sync(kFull, mbar_wait(acc_full + buf, accp[buf], abort_flag, a.status));
+          if (!w) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            float va[32], vb[32];
+            tmem_ld32_issue(tb + h * 64, va);
+            tmem_ld32_issue(tb + h * 64 + 32, vb);
+            tmem_ld_wait();
+            scan_chunk_coop<MC>(va, t * TC_ROWS + h * 64, rows_d, rows_i, thr, lane);
+            scan_chunk_coop<MC>(vb, t * TC_ROWS + h * 64 + 32, rows_d, rows_i, thr, lane);
+          }
+          tc_fence_before();
+          mbar_arrive(acc_empty + buf);
+          accp[buf] ^= 1u;
+          buf ^= 1;
+        }
+        if (!ok) break;
+        // write the 32 lists of this warp, one list per iteration (coalesced)
+        for (int L = 0; L < 32; ++L) {
+          const float qnL = __shfl_sync(kFull, qn, L);
+          const int64_t qL = q0 + L;
+          if (qL < a.nq && lane < MC) {
+            const float dv = rows_d[L * MC + lane];
+            const int iv = rows_i[L * MC + lane];
+            const bool real = iv >= 0 && iv < a.nd;
+            a.out_d[((int64_t)split * a.nq + qL) * MC + lane] = real ? qnL + dv : FLT_MAX;
+            a.out_id[((int64_t)split * a.nq + qL) * MC + lane] = real ? iv : -1;
+          }
+        }
+        __syncwarp();
+      }
+    } else
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;   // warp-uniform exit
       const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
