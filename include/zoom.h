@@ -184,6 +184,28 @@ zoom_status zoom_index_export(zoom_index ix, uint64_t* keys, int32_t* n_bins, vo
 zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, int32_t scale,
                          const zoom_upscale_params* prm, float* hr, void* stream);
 
+/* zoom_upscale_batch: zoom_upscale of n_images LR images of any sizes and of
+ * several scales in one call.  ixs: n_indexes index handles of one context,
+ * one per scale (image i uses the index whose dictionary has scale[i]).
+ * lr, hr: host arrays of n_images device pointers (hr[i] caller-allocated
+ * (scale[i]*h[i]) x (scale[i]*w[i])); h, w, scale: host arrays.  The
+ * queries of all images of one scale are concatenated and searched by one
+ * persistent launch.  On the first call for a set of images (same pointers,
+ * sizes and parameters), the search's dictionary split and list size are
+ * autotuned on a sample of the queries (CUDA events; synchronises), then
+ * every launch of the batch is recorded once into a CUDA graph; later calls
+ * with the same set only launch that graph on `stream` (the image contents
+ * may change).  per_image_ms (host, optional): device time from the start of
+ * the batch to the completion of image i (synchronises `stream`).  The
+ * recording keeps its scratch memory until zoom_batch_release, a call with
+ * a different set, or zoom_ctx_destroy. */
+zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t n_images,
+                               const float* const* lr, const int32_t* h, const int32_t* w,
+                               const int32_t* scale, const zoom_upscale_params* prm,
+                               float* const* hr, void* stream, float* per_image_ms);
+/* Frees the recorded batch of a context (synchronises the device). */
+zoom_status zoom_batch_release(zoom_ctx ctx);
+
 /* zoom_query: the per-patch steps only, for every LR patch origin (i, j) in
  * row order, n_q = (h-P+1)(w-P+1).  Outputs (device, any may be NULL except
  * nbr): keys uint64 [n_q][L] bucket keys of the query (Eq. 10 folded);

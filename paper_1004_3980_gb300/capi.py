@@ -74,6 +74,9 @@ SIGNATURES = {
     "zoom_set_stage_timing": (C.c_int, [_vp, C.c_int32]),
     "zoom_backproject_noalloc": (C.c_int, [C.c_int, _P(Degradation), _vp, _i32, _i32,
                                            _P(UpscaleParams), _vp, _vp]),
+    "zoom_upscale_batch": (C.c_int, [_P(_vp), _i32, _i32, _P(_vp), _P(_i32), _P(_i32), _P(_i32),
+                                     _P(UpscaleParams), _P(_vp), _vp, _P(_f)]),
+    "zoom_batch_release": (C.c_int, [_vp]),
     "zoom_degrade": (C.c_int, [_vp, _P(Degradation), _vp, _i32, _i32, _vp, _vp]),
     "zoom_degrade_adjoint": (C.c_int, [_vp, _P(Degradation), _vp, _i32, _i32, _vp, _vp]),
     "zoom_reconstruct_with": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -155,6 +156,7 @@ void zoom_ctx_destroy(zoom_ctx c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  zoom_release_batch(c);
   cudaFree(c->d_status);
   cudaFree(c->d_counters);
   cudaEventDestroy(c->ev0);
@@ -446,19 +448,23 @@ struct QueryBufs {
   int32_t* bucket_sum;
 };
 
-// Neighbour search: SIMT scan, or the tensor-core filter + exact rerank
-// (+ SIMT re-run of the queries the rerank could not settle).
-cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
-                       cudaStream_t st, bool& oom) {
+// How one neighbour search runs: the SIMT scan, or the tensor-core filter
+// with MC-entry lists over nsplit dictionary splits, and its scratch size.
+struct SearchPlan {
+  bool tc = false;
+  int prec = 0, MC = 16, nsplit = 1, KCH = 80;
+  int64_t q_rows = 0;
+  size_t bytes = 0;
+};
+
+SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq, int nsplit_override,
+                       int mc_override) {
   zoom_dict d = ix->dict;
-  zoom_ctx ctx = d->ctx;
-  const int K = prm->K;
-  const bool tc = prm->precision == 1 || prm->search == 2 || (prm->search == 0 && d->n >= 4096);
-  if (!tc)
-    return launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, nullptr,
-                            nullptr, st);
-  const int prec = prm->precision;
-  const int MC = tc_list_size(prec, K, prm->rerank_mult);
+  SearchPlan p;
+  p.tc = prm->precision == 1 || prm->search == 2 || (prm->search == 0 && d->n >= 4096);
+  if (!p.tc) return p;
+  p.prec = prm->precision;
+  p.MC = mc_override > 0 ? mc_override : tc_list_size(p.prec, prm->K, prm->rerank_mult);
   const int64_t nd_tiles = ix->nd_rows / 128;
   const int64_t nq_pairs = (nq + 255) / 256;
   // Every CTA streams the dictionary tiles in the same order at about the
@@ -466,39 +472,61 @@ cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const Quer
   // A split restarts every query's best list (about MC*ln(N/MC) insertions
   // each), so the dictionary is split only as far as needed to give every SM
   // (query pair, split) items.
-  int64_t nsplit = (2ll * ctx->n_sm + nq_pairs - 1) / nq_pairs;
-  nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
-  const int64_t q_rows = tc_rows_padded(nq, true);
-  const int KCH = prec == 0 ? 80 : 32;
+  int64_t nsplit = nsplit_override > 0 ? nsplit_override : (2ll * d->ctx->n_sm + nq_pairs - 1) / nq_pairs;
+  p.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
+  p.q_rows = tc_rows_padded(nq, true);
+  p.KCH = p.prec == 0 ? 80 : 32;
   Carver c(nullptr);
-  c.take<uint16_t>(q_rows * KCH);
+  c.take<uint16_t>(p.q_rows * p.KCH);
   c.take<float>(nq);
-  c.take<float>(nsplit * nq * MC);
-  c.take<int32_t>(nsplit * nq * MC);
+  c.take<float>((size_t)p.nsplit * nq * p.MC);
+  c.take<int32_t>((size_t)p.nsplit * nq * p.MC);
   c.take<int32_t>(nq);
-  Scratch scr(ctx, st);
-  if (!scr.get(c.off + 256)) {
-    oom = true;
-    return cudaSuccess;
-  }
-  Carver s2(scr.p);
-  uint16_t* qop = s2.take<uint16_t>(q_rows * KCH);
+  p.bytes = c.off + 256;
+  return p;
+}
+
+// Neighbour search with a caller-provided workspace of plan.bytes: SIMT
+// scan, or the tensor-core filter + exact rerank (+ SIMT re-run of the
+// queries the rerank could not settle).  Allocates nothing.
+cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
+                          const SearchPlan& pl, void* ws, cudaStream_t st) {
+  zoom_dict d = ix->dict;
+  zoom_ctx ctx = d->ctx;
+  const int K = prm->K;
+  if (!pl.tc)
+    return launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, nullptr,
+                            nullptr, st);
+  Carver s2(ws);
+  uint16_t* qop = s2.take<uint16_t>(pl.q_rows * pl.KCH);
   float* qn = s2.take<float>(nq);
-  float* ld = s2.take<float>(nsplit * nq * MC);
-  int32_t* li = s2.take<int32_t>(nsplit * nq * MC);
+  float* ld = s2.take<float>((size_t)pl.nsplit * nq * pl.MC);
+  int32_t* li = s2.take<int32_t>((size_t)pl.nsplit * nq * pl.MC);
   int32_t* fb = s2.take<int32_t>(nq);
-  cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, q_rows, 0, prec, qop, qn, st);
+  cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
   if (e == cudaSuccess)
-    e = launch_knn_tc(qop, qn, nq, prec == 0 ? ix->dop16 : ix->dopbf, d->n, prec, MC, (int)nsplit,
-                      ctx->n_sm, ld, li, ctx->d_status, st);
+    e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.MC,
+                      pl.nsplit, ctx->n_sm, ld, li, ctx->d_status, st);
   if (e == cudaSuccess)
-    e = launch_rerank(d->d, MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
-                      ix->t, ld, li, (int)nsplit, prec == 0 ? 1 : 0, prm->rerank_mult * K, b.nbr,
+    e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
+                      ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : 0, prm->rerank_mult * K, b.nbr,
                       b.dist, fb, ctx->d_counters, st);
   if (e == cudaSuccess)
     e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
                          ctx->d_counters + CNT_FALLBACK, st);
   return e;
+}
+
+cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
+                       cudaStream_t st, bool& oom) {
+  const SearchPlan pl = plan_search(ix, prm, nq, 0, 0);
+  if (!pl.tc) return run_search_ws(ix, prm, b, nq, pl, nullptr, st);
+  Scratch scr(ix->dict->ctx, st);
+  if (!scr.get(pl.bytes)) {
+    oom = true;
+    return cudaSuccess;
+  }
+  return run_search_ws(ix, prm, b, nq, pl, scr.p, st);
 }
 
 zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
@@ -731,6 +759,370 @@ zoom_status zoom_sync_status(zoom_ctx ctx, void* stream) {
   ZCHECK_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
   if (v == 1) return fail(ZOOM_ERR_TIMEOUT, "a device wait gave up");
   return fail(ZOOM_ERR_DEVICE, "device status word " + std::to_string(v));
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched zoom: one call for many LR images, recorded into a CUDA graph
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Search choices picked by the autotuner, per (index, query count bucket,
+// precision, K).
+struct TuneKey {
+  const void* ix;
+  int64_t qbucket;
+  int prec, K;
+  bool operator<(const TuneKey& o) const {
+    if (ix != o.ix) return ix < o.ix;
+    if (qbucket != o.qbucket) return qbucket < o.qbucket;
+    if (prec != o.prec) return prec < o.prec;
+    return K < o.K;
+  }
+};
+struct TuneChoice {
+  int nsplit = 0, mc = 0;
+  float ms = 0.f;
+};
+using TuneMap = std::map<TuneKey, TuneChoice>;
+
+struct Group {
+  zoom_index ix = nullptr;
+  std::vector<int> images;
+  std::vector<int64_t> q_off;   // query offset of each image in the group
+  int64_t nq = 0;
+  SearchPlan plan;
+  QueryBufs b{};
+  void* ws = nullptr;
+};
+
+struct BatchRecord {
+  std::vector<int64_t> key;
+  void* mem = nullptr;           // query buffers and back-projection scratch
+  size_t bytes = 0;
+  void* ws = nullptr;            // search scratch of every group
+  size_t ws_bytes = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaEvent_t> ev;   // [0] start, [1 + i] end of image i
+  std::vector<Group> groups;
+};
+
+void free_record(zoom_ctx ctx, BatchRecord* r) {
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
+  if (r->cap) cudaStreamDestroy(r->cap);
+  if (r->mem) zoom_free(ctx, r->mem, r->bytes, nullptr);
+  if (r->ws) zoom_free(ctx, r->ws, r->ws_bytes, nullptr);
+  delete r;
+}
+
+}  // namespace
+
+void zoom_release_batch(zoom_ctx ctx) {
+  if (ctx->batch) {
+    cudaDeviceSynchronize();
+    free_record(ctx, (BatchRecord*)ctx->batch);
+    ctx->batch = nullptr;
+  }
+  delete (TuneMap*)ctx->tuned;
+  ctx->tuned = nullptr;
+}
+
+namespace {
+
+void release_batch(zoom_ctx ctx) {
+  BatchRecord* r = (BatchRecord*)ctx->batch;
+  if (!r) return;
+  cudaDeviceSynchronize();   // the recorded graph may still run on the caller's stream
+  free_record(ctx, r);
+  ctx->batch = nullptr;
+}
+
+int64_t qbucket(int64_t nq) {
+  int64_t b = 1;
+  while (b < nq) b <<= 1;
+  return b;
+}
+
+// Times each candidate (splits x list size) of one group's search on a
+// sample of its queries and remembers the fastest.
+zoom_status autotune_group(Group& g, const zoom_upscale_params* prm, cudaStream_t st) {
+  zoom_ctx ctx = g.ix->dict->ctx;
+  TuneMap& tm = *(TuneMap*)ctx->tuned;
+  const TuneKey key{g.ix, qbucket(g.nq), prm->precision, prm->K};
+  if (tm.count(key)) return ZOOM_OK;
+  const int64_t ns = std::min<int64_t>(g.nq, 131072);
+  std::vector<std::pair<int, int>> cands;
+  const int mc0 = tc_list_size(prm->precision, prm->K, prm->rerank_mult);
+  for (int s : {0, 1, 2, 4}) {
+    cands.push_back({s, mc0});
+    if (prm->precision == 0 && mc0 == 16) cands.push_back({s, 32});
+  }
+  TuneChoice best;
+  best.ms = 1e30f;
+  cudaEvent_t e0, e1;
+  ZCHECK_CUDA(cudaEventCreate(&e0));
+  ZCHECK_CUDA(cudaEventCreate(&e1));
+  for (auto& c : cands) {
+    const SearchPlan pl = plan_search(g.ix, prm, ns, c.first, c.second);
+    Scratch scr(ctx, st);
+    if (!scr.get(pl.bytes)) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+      cudaEventRecord(e0, st);
+      cudaError_t e = run_search_ws(g.ix, prm, g.b, ns, pl, scr.p, st);
+      cudaEventRecord(e1, st);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(ZOOM_ERR_CUDA, "autotune search failed");
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ms < best.ms) {
+      best.ms = ms;
+      best.nsplit = c.first;
+      best.mc = c.second;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tm[key] = best;
+  return ZOOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t n_images,
+                               const float* const* lr, const int32_t* h, const int32_t* w,
+                               const int32_t* scale, const zoom_upscale_params* prm,
+                               float* const* hr, void* stream, float* per_image_ms) {
+  if (!ixs || n_indexes < 1 || n_images < 1 || !lr || !h || !w || !scale || !prm || !hr)
+    return fail(ZOOM_ERR_INVALID_ARG, "NULL or empty argument");
+  zoom_ctx ctx = ixs[0] ? ixs[0]->dict->ctx : nullptr;
+  if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL index");
+  for (int j = 0; j < n_indexes; ++j) {
+    if (!ixs[j]) return fail(ZOOM_ERR_INVALID_ARG, "NULL index");
+    if (ixs[j]->dict->ctx != ctx) return fail(ZOOM_ERR_INVALID_ARG, "indexes of different contexts");
+    std::string why;
+    if (!check_upscale_params(prm, ixs[j]->dict, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  cudaGetLastError();   // launch checks below read the runtime's last error
+  // group the images by the index whose dictionary has their scale
+  std::vector<Group> groups(n_indexes);
+  std::vector<int64_t> key;
+  key.push_back(n_images);
+  for (int j = 0; j < n_indexes; ++j) {
+    groups[j].ix = ixs[j];
+    key.push_back((int64_t)(uintptr_t)ixs[j]);
+  }
+  for (int i = 0; i < n_images; ++i) {
+    int g = -1;
+    for (int j = 0; j < n_indexes; ++j)
+      if (ixs[j]->dict->s == scale[i]) g = j;
+    if (g < 0) return fail(ZOOM_ERR_INVALID_ARG, "no index for the scale of image " + std::to_string(i));
+    zoom_dict d = ixs[g]->dict;
+    if (!lr[i] || !hr[i] || h[i] < d->P || w[i] < d->P)
+      return fail(ZOOM_ERR_INVALID_ARG, "bad image " + std::to_string(i));
+    groups[g].images.push_back(i);
+    groups[g].q_off.push_back(groups[g].nq);
+    groups[g].nq += (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1);
+    for (int64_t v : {(int64_t)(uintptr_t)lr[i], (int64_t)(uintptr_t)hr[i], (int64_t)h[i], (int64_t)w[i],
+                      (int64_t)scale[i]})
+      key.push_back(v);
+  }
+  for (int64_t v : {(int64_t)prm->K, (int64_t)prm->bp_iters, (int64_t)prm->precision,
+                    (int64_t)prm->rerank_mult, (int64_t)prm->search, (int64_t)prm->bp_radius,
+                    (int64_t)(prm->reg_rel * 1e9f), (int64_t)(prm->sigma_spatial * 1e6f),
+                    (int64_t)(prm->sigma_range * 1e6f)})
+    key.push_back(v);
+  if (!ctx->tuned) ctx->tuned = new TuneMap();
+  BatchRecord* rec = (BatchRecord*)ctx->batch;
+  if (!rec || rec->key != key) {
+    release_batch(ctx);
+    rec = new BatchRecord();
+    rec->key = key;
+    // workspace: per group the query buffers and the search scratch, per
+    // image the back-projection scratch
+    int64_t max_hw = 0;
+    for (int i = 0; i < n_images; ++i) max_hw = std::max<int64_t>(max_hw, (int64_t)h[i] * w[i] * scale[i] * scale[i]);
+    Carver c(nullptr);
+    for (auto& g : groups) {
+      if (g.images.empty()) continue;
+      zoom_dict d = g.ix->dict;
+      c.take<float>(g.nq * d->dpad);
+      c.take<float>(g.nq);
+      c.take<uint64_t>(g.nq * g.ix->L);
+      c.take<int32_t>(g.nq * prm->K);
+      c.take<float>(g.nq * prm->K);
+      c.take<float>(g.nq * prm->K);
+      c.take<char>(0);
+    }
+    for (int i = 0; i < n_images; ++i) {
+      c.take<float>((size_t)h[i] * w[i] * scale[i] * scale[i]);
+      c.take<float>((size_t)h[i] * w[i]);
+    }
+    const size_t base_bytes = c.off + 256;
+    // the query buffers first (the autotuner needs features and keys)
+    rec->bytes = base_bytes;
+    rec->mem = zoom_alloc(ctx, rec->bytes, st);
+    if (!rec->mem) {
+      delete rec;
+      return fail(ZOOM_ERR_OOM, "batch workspace");
+    }
+    Carver m(rec->mem);
+    for (auto& g : groups) {
+      if (g.images.empty()) continue;
+      zoom_dict d = g.ix->dict;
+      g.b.feat = m.take<float>(g.nq * d->dpad);
+      g.b.mu = m.take<float>(g.nq);
+      g.b.norm2 = nullptr;
+      g.b.keys = m.take<uint64_t>(g.nq * g.ix->L);
+      g.b.nbr = m.take<int32_t>(g.nq * prm->K);
+      g.b.dist = m.take<float>(g.nq * prm->K);
+      g.b.wgt = m.take<float>(g.nq * prm->K);
+      g.b.bucket_sum = nullptr;
+      m.take<char>(0);
+    }
+    std::vector<float*> tmp(n_images), err(n_images);
+    for (int i = 0; i < n_images; ++i) {
+      tmp[i] = m.take<float>((size_t)h[i] * w[i] * scale[i] * scale[i]);
+      err[i] = m.take<float>((size_t)h[i] * w[i]);
+    }
+    // features and keys of every image, then one autotuning pass per group
+    for (auto& g : groups) {
+      zoom_dict d = g.ix->dict;
+      for (size_t k = 0; k < g.images.size(); ++k) {
+        const int i = g.images[k];
+        const int64_t o = g.q_off[k];
+        cudaError_t e = launch_query_features(lr[i], h[i], w[i], d->P, d->dpad, g.b.feat + o * d->dpad,
+                                              g.b.mu + o, nullptr, st);
+        const int64_t nqi = (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1);
+        if (e == cudaSuccess)
+          e = launch_hash(g.b.feat + o * d->dpad, d->dpad, d->d, nqi, g.ix->alpha, g.ix->beta, g.ix->L,
+                          g.ix->k, g.ix->w, g.b.keys + o * g.ix->L, st);
+        if (e != cudaSuccess) {
+          free_record(ctx, rec);
+          return fail(ZOOM_ERR_CUDA, std::string("batch features: ") + cudaGetErrorString(e));
+        }
+      }
+      if (!g.images.empty() && plan_search(g.ix, prm, g.nq, 0, 0).tc) {
+        zoom_status rs = autotune_group(g, prm, st);
+        if (rs != ZOOM_OK) {
+          free_record(ctx, rec);
+          return rs;
+        }
+      }
+    }
+    // search scratch per group, with the tuned plan
+    size_t extra = 0;
+    TuneMap& tm = *(TuneMap*)ctx->tuned;
+    for (auto& g : groups) {
+      if (g.images.empty()) continue;
+      const TuneKey tk{g.ix, qbucket(g.nq), prm->precision, prm->K};
+      const TuneChoice ch = tm.count(tk) ? tm[tk] : TuneChoice();
+      g.plan = plan_search(g.ix, prm, g.nq, ch.nsplit, ch.mc);
+      extra += (g.plan.bytes + 255) / 256 * 256;
+    }
+    void* ws = extra ? zoom_alloc(ctx, extra, st) : nullptr;
+    if (extra && !ws) {
+      free_record(ctx, rec);
+      return fail(ZOOM_ERR_OOM, "batch search workspace");
+    }
+    rec->ws = ws;
+    rec->ws_bytes = extra;
+    {
+      char* p = (char*)ws;
+      for (auto& g : groups) {
+        if (g.images.empty()) continue;
+        g.ws = p;
+        p += (g.plan.bytes + 255) / 256 * 256;
+      }
+    }
+    // record the whole batch on a private stream into a graph
+    ZCHECK_CUDA(cudaStreamCreateWithFlags(&rec->cap, cudaStreamNonBlocking));
+    rec->ev.resize(n_images + 1);
+    for (auto& e : rec->ev) ZCHECK_CUDA(cudaEventCreate(&e));
+    cudaStream_t cs = rec->cap;
+    ZCHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // external records become event nodes of the graph (readable timings)
+    cudaError_t e = cudaEventRecordWithFlags(rec->ev[0], cs, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counters, 0, CNT_N * sizeof(unsigned long long), cs);
+    for (auto& g : groups) {
+      if (g.images.empty() || e != cudaSuccess) continue;
+      zoom_dict d = g.ix->dict;
+      for (size_t k = 0; k < g.images.size() && e == cudaSuccess; ++k) {
+        const int i = g.images[k];
+        const int64_t o = g.q_off[k];
+        const int64_t nqi = (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1);
+        e = launch_query_features(lr[i], h[i], w[i], d->P, d->dpad, g.b.feat + o * d->dpad, g.b.mu + o,
+                                  nullptr, cs);
+        if (e == cudaSuccess)
+          e = launch_hash(g.b.feat + o * d->dpad, d->dpad, d->d, nqi, g.ix->alpha, g.ix->beta, g.ix->L,
+                          g.ix->k, g.ix->w, g.b.keys + o * g.ix->L, cs);
+      }
+      // one search over the concatenated queries of every image of this scale
+      if (e == cudaSuccess) e = run_search_ws(g.ix, prm, g.b, g.nq, g.plan, g.ws, cs);
+      if (e == cudaSuccess)
+        e = launch_lle(d, g.b.feat, g.nq, g.b.nbr, g.b.dist, prm->K, prm->reg_rel, prm->fp64_cond_threshold,
+                       g.b.wgt, ctx->d_counters, cs);
+      for (size_t k = 0; k < g.images.size() && e == cudaSuccess; ++k) {
+        const int i = g.images[k];
+        const int64_t o = g.q_off[k];
+        e = launch_overlap_add(g.b.nbr + o * prm->K, g.b.wgt + o * prm->K, g.b.mu + o, d->hr_res, d->ph2pad,
+                               prm->K, h[i], w[i], d->s, d->P, hr[i], cs);
+        float* a = hr[i];
+        float* bb = tmp[i];
+        for (int it = 0; it < prm->bp_iters && e == cudaSuccess; ++it) {
+          e = launch_bp_iteration(a, bb, lr[i], err[i], h[i], w[i], d->s, d->blur_sigma, prm->sigma_spatial,
+                                  prm->sigma_range, prm->bp_radius, cs);
+          std::swap(a, bb);
+        }
+        if (e == cudaSuccess && a != hr[i])
+          e = cudaMemcpyAsync(hr[i], a, (size_t)h[i] * w[i] * d->s * d->s * 4, cudaMemcpyDeviceToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(rec->ev[1 + i], cs, cudaEventRecordExternal);
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&rec->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    rec->groups = groups;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_record(ctx, rec);
+      return fail(ZOOM_ERR_CUDA, std::string("batch recording: ") + cudaGetErrorString(e));
+    }
+    ctx->batch = rec;
+  }
+  ZCHECK_CUDA(cudaGraphLaunch(rec->exec, st));
+  ctx->last_n_queries = 0;
+  for (auto& g : rec->groups)
+    if (g.ix) ctx->last_n_queries += g.nq;
+  if (per_image_ms) {
+    ZCHECK_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_images; ++i) {
+      float ms = 0.f;
+      ZCHECK_CUDA(cudaEventElapsedTime(&ms, rec->ev[0], rec->ev[1 + i]));
+      per_image_ms[i] = ms;
+    }
+  }
+  return ZOOM_OK;
+}
+
+zoom_status zoom_batch_release(zoom_ctx ctx) {
+  if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL context");
+  ZCHECK_CUDA(cudaSetDevice(ctx->device));
+  zoom_release_batch(ctx);
+  return ZOOM_OK;
 }
 
 }  // extern "C"

@@ -35,10 +35,14 @@ struct zoom_ctx_s {
   bool stage_timing = false;
   cudaEvent_t stage_ev[9] = {};   // boundaries of the 7 stages (+1 spare)
   bool stage_rec[9] = {};
+  void* batch = nullptr;          // recorded batch (graph, workspace, events): zoom_api.cu
+  void* tuned = nullptr;          // autotuned search choices: zoom_api.cu
 };
 
 // Records the boundary event of stage `i` when stage timing is on.
 void zoom_stage_mark(zoom_ctx ctx, int i, cudaStream_t st);
+// Frees the context's recorded batch and autotuning choices.
+void zoom_release_batch(zoom_ctx ctx);
 
 struct zoom_dict_s {
   zoom_ctx ctx = nullptr;

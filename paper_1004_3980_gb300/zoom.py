@@ -379,3 +379,46 @@ def map_energy_grads(index: Index, lr: torch.Tensor, nbr: torch.Tensor, wgt: tor
     capi.call("zoom_backward", index.handle, _ptr(lr), h, w, _ptr(nbr), _ptr(wgt), nbr.shape[1], reg_rel, lam,
               _ptr(gx), _ptr(gd), ph2, _ptr(x), C.byref(e), _stream(stream))
     return {"energy": e.value, "grad_x": gx, "grad_dict": gd, "hr": x}
+
+
+# ---------------------------------------------------------------------------
+# batched zoom
+# ---------------------------------------------------------------------------
+
+
+def upscale_batch(indexes, lrs, params: UpscaleParams | None = None, outs=None, want_latency: bool = False,
+                  stream=None):
+    """Zoom many LR images (CUDA float32, any sizes) in one call.  `lrs` is a
+    list of (scale, lr) pairs (or plain tensors, all at the scale of
+    indexes[0]); each image uses the index whose dictionary has its scale.
+    Returns (outputs, per-image device ms from the batch start, or None)."""
+    p = params or UpscaleParams()
+    if isinstance(lrs[0], tuple):
+        scales = [s for s, _ in lrs]
+        lrs = [x for _, x in lrs]
+    else:
+        scales = [indexes[0].dictionary.scale] * len(lrs)
+    by_scale = {ix.dictionary.scale: ix for ix in indexes}
+    if outs is None:
+        outs = [torch.empty((s * x.shape[0], s * x.shape[1]), dtype=torch.float32, device=x.device)
+                for s, x in zip(scales, lrs)]
+    for x in lrs:
+        _need(x, torch.float32, "lr")
+    n = len(lrs)
+    ix_arr = (C.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    lr_arr = (C.c_void_p * n)(*[x.data_ptr() for x in lrs])
+    hr_arr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    hs = (C.c_int32 * n)(*[x.shape[0] for x in lrs])
+    ws = (C.c_int32 * n)(*[x.shape[1] for x in lrs])
+    ss = (C.c_int32 * n)(*scales)
+    lat = (C.c_float * n)() if want_latency else None
+    if any(s not in by_scale for s in scales):
+        raise ValueError("no index for some image's scale")
+    cp = p.c()
+    capi.call("zoom_upscale_batch", ix_arr, len(indexes), n, lr_arr, hs, ws, ss, C.byref(cp), hr_arr,
+              _stream(stream), lat)
+    return outs, (list(lat) if want_latency else None)
+
+
+def batch_release(ctx: Context) -> None:
+    capi.call("zoom_batch_release", ctx.handle)
