@@ -125,7 +125,8 @@ typedef struct {
   double ms_total;          /* device time of the last call (CUDA events)     */
   /* per-stage device milliseconds of the last call, when stage timing is on:
    * [0] features, [1] hashing, [2] bin lookup, [3] neighbour search,
-   * [4] LLE solve, [5] blend + overlap average, [6] back-projection */
+   * [4] LLE solve, [5] blend + overlap average, [6] back-projection,
+   * [7] the tensor-core filter kernel alone (within [3]; 0 on the SIMT scan) */
   double ms_stage[8];
 } zoom_stats;
 

@@ -79,7 +79,7 @@ bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string
 void zoom_set_error(const std::string& msg) { g_last_error = msg; }
 
 void zoom_stage_mark(zoom_ctx ctx, int i, cudaStream_t st) {
-  if (!ctx->stage_timing || i < 0 || i > 8) return;
+  if (!ctx->stage_timing || i < 0 || i >= kStageEvents) return;
   if (cudaEventRecord(ctx->stage_ev[i], st) == cudaSuccess) ctx->stage_rec[i] = true;
 }
 
@@ -147,7 +147,7 @@ zoom_status zoom_ctx_create(int device, const zoom_allocator* alloc, zoom_ctx* o
   cudaMemset(c->d_counters, 0, CNT_N * sizeof(unsigned long long));
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
-  for (int i = 0; i < 9; ++i) cudaEventCreate(&c->stage_ev[i]);
+  for (int i = 0; i < kStageEvents; ++i) cudaEventCreate(&c->stage_ev[i]);
   *out = c;
   return ZOOM_OK;
 }
@@ -161,7 +161,7 @@ void zoom_ctx_destroy(zoom_ctx c) {
   cudaFree(c->d_counters);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
-  for (int i = 0; i < 9; ++i) cudaEventDestroy(c->stage_ev[i]);
+  for (int i = 0; i < kStageEvents; ++i) cudaEventDestroy(c->stage_ev[i]);
   delete c;
 }
 
@@ -504,9 +504,11 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   int32_t* li = s2.take<int32_t>((size_t)pl.nsplit * nq * pl.MC);
   int32_t* fb = s2.take<int32_t>(nq);
   cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
+  zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
     e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.MC,
                       pl.nsplit, ctx->n_sm, ld, li, ctx->d_status, st);
+  zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
                       ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : 0, prm->rerank_mult * K, b.nbr,
@@ -556,7 +558,7 @@ zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
 
 zoom_status begin_call(zoom_ctx ctx, int64_t nq, cudaStream_t st) {
   ZCHECK_CUDA(cudaSetDevice(ctx->device));
-  for (int i = 0; i < 9; ++i) ctx->stage_rec[i] = false;
+  for (int i = 0; i < kStageEvents; ++i) ctx->stage_rec[i] = false;
   ZCHECK_CUDA(cudaMemsetAsync(ctx->d_counters, 0, CNT_N * sizeof(unsigned long long), st));
   ZCHECK_CUDA(cudaEventRecord(ctx->ev0, st));
   ctx->last_n_queries = nq;
@@ -731,6 +733,14 @@ zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out) {
     if (ctx->stage_rec[i] && ctx->stage_rec[i + 1] &&
         cudaEventElapsedTime(&ms, ctx->stage_ev[i], ctx->stage_ev[i + 1]) == cudaSuccess)
       out->ms_stage[i] = ms;
+    else
+      cudaGetLastError();
+  }
+  {
+    float ms = 0.f;   // the tensor-core filter kernel alone
+    if (ctx->stage_rec[8] && ctx->stage_rec[9] &&
+        cudaEventElapsedTime(&ms, ctx->stage_ev[8], ctx->stage_ev[9]) == cudaSuccess)
+      out->ms_stage[7] = ms;
     else
       cudaGetLastError();
   }

@@ -22,6 +22,8 @@ enum CounterSlot {
   CNT_N = 8
 };
 
+constexpr int kStageEvents = 10;
+
 struct zoom_ctx_s {
   int device = 0;
   int n_sm = 0;
@@ -33,8 +35,9 @@ struct zoom_ctx_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
   bool stage_timing = false;
-  cudaEvent_t stage_ev[9] = {};   // boundaries of the 7 stages (+1 spare)
-  bool stage_rec[9] = {};
+  // boundaries of the 7 stages (0..7) and of the tensor-core filter kernel (8, 9)
+  cudaEvent_t stage_ev[kStageEvents] = {};
+  bool stage_rec[kStageEvents] = {};
   void* batch = nullptr;          // recorded batch (graph, workspace, events): zoom_api.cu
   void* tuned = nullptr;          // autotuned search choices: zoom_api.cu
 };

@@ -34,7 +34,7 @@ def _finalizing() -> bool:
     return sys.is_finalizing()
 
 
-STAGES = ("features", "hash", "lookup", "knn", "lle", "overlap_add", "backproject")
+STAGES = ("features", "hash", "lookup", "knn", "lle", "overlap_add", "backproject", "knn_filter_kernel")
 
 
 def _stream(stream=None) -> C.c_void_p:
