@@ -98,6 +98,11 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
   atomicExch(status, 1u);
   return false;
 }
+// The common case inline: one poll, then the bounded slow path.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned int* status) {
+  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag, status);
+}
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -260,6 +265,28 @@ __device__ __forceinline__ void flush_appends(float (&ld)[MC], int (&li)[MC], fl
   cnt = 0;
 }
 
+// Three-input minimum (sm_100 family): halves the instructions of a
+// reduction.  The accumulator values are finite.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+// Minimum of 8 consecutive values v[o..o+7].
+__device__ __forceinline__ float min8(const float (&v)[32], int o) {
+  return fmin3(fmin3(v[o], v[o + 1], v[o + 2]), fmin3(v[o + 3], v[o + 4], v[o + 5]), fminf(v[o + 6], v[o + 7]));
+}
+// Minimum of the 32 values (16 instructions).
+__device__ __forceinline__ float min32(const float (&v)[32]) {
+  float a[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) a[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+  a[10] = fminf(v[30], v[31]);
+  const float b0 = fmin3(a[0], a[1], a[2]), b1 = fmin3(a[3], a[4], a[5]);
+  const float b2 = fmin3(a[6], a[7], a[8]);
+  return fmin3(fmin3(b0, b1, b2), a[9], a[10]);
+}
+
 // One 32-column chunk of a query's accumulator row: the chunk minimum is
 // compared with the list threshold; columns below it are appended.
 template <int MC>
@@ -267,20 +294,12 @@ __device__ __forceinline__ void scan_chunk(const float (&v)[32], int col0, float
                                            float& thr, float* bv, int* bi, int& cnt) {
   // room for the up to 32 appends of this chunk in every lane
   if (__any_sync(0xffffffffu, cnt > kBuf - 32)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
-  float gm[4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    gm[g] = v[g * 8];
-#pragma unroll
-    for (int j = 1; j < 8; ++j) gm[g] = fminf(gm[g], v[g * 8 + j]);
-  }
-  const float m = fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3]));
-  if (m < thr) {
+  if (min32(v) < thr) {
     // rare: append the columns below the (possibly stale) threshold to this
     // lane's buffer; they are merged into the list later, by the whole warp
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-      if (gm[g] < thr) {
+      if (min8(v, g * 8) < thr) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float x = v[g * 8 + j];
@@ -337,12 +356,8 @@ __device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], int col0, 
                                                 float& thr, int lane) {
   float gm[4];
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    gm[g] = v[g * 8];
-#pragma unroll
-    for (int j = 1; j < 8; ++j) gm[g] = fminf(gm[g], v[g * 8 + j]);
-  }
-  const float m = fminf(fminf(gm[0], gm[1]), fminf(gm[2], gm[3]));
+  for (int g = 0; g < 4; ++g) gm[g] = min8(v, g * 8);
+  const float m = fmin3(gm[0], gm[1], fminf(gm[2], gm[3]));
   unsigned hit = __ballot_sync(kFull, m < thr);
   while (hit) {                                 // warp-uniform from here on
     const int L = __ffs(hit) - 1;
@@ -449,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         mbar_arrive_expect_tx(a_full, 2 * kTileBytes);
         bulk_g2s(sA, (const unsigned char*)a.qop + (size_t)qp * 2 * kTileBytes, 2 * kTileBytes, a_full);
         for (int t = t0; t < t1; ++t) {
-          if (!mbar_wait(b_empty + stage, phase ^ 1u, abort_flag, a.status)) break;
+          if (!mbar_wait_fast(b_empty + stage, phase ^ 1u, abort_flag, a.status)) break;
           mbar_arrive_expect_tx(b_full + stage, kTileBytes);
           bulk_g2s(sB + stage * kTileBytes, (const unsigned char*)a.dop + (size_t)t * kTileBytes,
                    kTileBytes, b_full + stage);
@@ -466,32 +481,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
       int stage = 0, buf = 0, items = 0;
       uint32_t phase = 0, a_phase = 0;
       uint32_t accp[2] = {0u, 0u};
+      // Descriptors of the first K step of both query tiles and of ring
+      // stage 0; a K step adds 2 core-matrix columns (4 KiB), a stage one tile
+      // (start address field in 16-byte units; every address stays below
+      // 256 KiB, so the 14-bit field never carries).
+      const uint64_t ad0 = smem_desc(smem_u32(sA), TC_ROWS * 16, 128);
+      const uint64_t bd0 = smem_desc(smem_u32(sB), TC_ROWS * 16, 128);
+      constexpr uint64_t kKStepAdv = (2 * TC_ROWS * 16) >> 4;
+      constexpr uint64_t kTileAdv = kTileBytes >> 4;
       for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
         const int split = item / a.nq_pairs;
         const int t0 = split * a.tiles_per_split;
         const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
-        if (!mbar_wait(a_full, a_phase, abort_flag, a.status)) break;
+        if (!mbar_wait_fast(a_full, a_phase, abort_flag, a.status)) break;
         a_phase ^= 1u;
         tc_fence_after();
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
-          if (!mbar_wait(b_full + stage, phase, abort_flag, a.status) ||
-              !mbar_wait(acc_empty + buf, accp[buf] ^ 1u, abort_flag, a.status)) {
+          if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status) ||
+              !mbar_wait_fast(acc_empty + buf, accp[buf] ^ 1u, abort_flag, a.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t b_base = smem_u32(sB + stage * kTileBytes);
+          const uint64_t bd_s = bd0 + (uint64_t)stage * kTileAdv;
 #pragma unroll
           for (int qt = 0; qt < 2; ++qt) {
-            const uint32_t a_base = smem_u32(sA + qt * kTileBytes);
             const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
 #pragma unroll
-            for (int ks = 0; ks < kKSteps; ++ks) {
-              const uint64_t ad = smem_desc(a_base + ks * 2 * TC_ROWS * 16, TC_ROWS * 16, 128);
-              const uint64_t bd = smem_desc(b_base + ks * 2 * TC_ROWS * 16, TC_ROWS * 16, 128);
-              mma_f16(d_addr, ad, bd, kIdesc, ks > 0 ? 1u : 0u);
-            }
+            for (int ks = 0; ks < kKSteps; ++ks)
+              mma_f16(d_addr, ad0 + (uint64_t)qt * kTileAdv + ks * kKStepAdv, bd_s + ks * kKStepAdv, kIdesc,
+                      ks > 0 ? 1u : 0u);
           }
           mma_commit(b_empty + stage);
           mma_commit(acc_full + buf);
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         float thr = FLT_MAX;
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
-          const bool w = __all_sync(kFull, mbar_wait(acc_full + buf, accp[buf], abort_flag, a.status));
+          const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf, accp[buf], abort_flag, a.status));
           if (!w) {
             ok = false;
             break;
@@ -554,11 +574,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
             tmem_ld32_issue(tb + h * 64, va);
             tmem_ld32_issue(tb + h * 64 + 32, vb);
             tmem_ld_wait();
+            if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+              tc_fence_before();
+              mbar_arrive(acc_empty + buf);
+            }
             scan_chunk_coop<MC>(va, t * TC_ROWS + h * 64, rows_d, rows_i, thr, lane);
             scan_chunk_coop<MC>(vb, t * TC_ROWS + h * 64 + 32, rows_d, rows_i, thr, lane);
           }
-          tc_fence_before();
-          mbar_arrive(acc_empty + buf);
           accp[buf] ^= 1u;
           buf ^= 1;
         }
@@ -599,7 +621,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
         // warp-collective TMEM loads
-        const bool w = __all_sync(0xffffffffu, mbar_wait(acc_full + buf, accp[buf], abort_flag, a.status));
+        const bool w = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + buf, accp[buf], abort_flag, a.status));
         if (!w) {
           ok = false;
           break;
@@ -614,6 +636,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
             tmem_ld32_issue(tb + h * 64, va);
             tmem_ld32_issue(tb + h * 64 + 32, vb);
             tmem_ld_wait();
+            if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+              tc_fence_before();
+              mbar_arrive(acc_empty + buf);
+            }
             scan_chunk<MC>(va, t * TC_ROWS + h * 64, ld, li, thr, bv, bi, cnt);
             scan_chunk<MC>(vb, t * TC_ROWS + h * 64 + 32, ld, li, thr, bv, bi, cnt);
           }
@@ -624,11 +650,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
             float v[32];
             tmem_ld32_issue(tb + c * 32, v);
             tmem_ld_wait();
+            if (c == 3) {
+              tc_fence_before();
+              mbar_arrive(acc_empty + buf);
+            }
             scan_chunk<MC>(v, t * TC_ROWS + c * 32, ld, li, thr, bv, bi, cnt);
           }
         }
-        tc_fence_before();
-        mbar_arrive(acc_empty + buf);
         accp[buf] ^= 1u;
         buf ^= 1;
       }

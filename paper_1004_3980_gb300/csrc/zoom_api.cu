@@ -469,10 +469,27 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   const int64_t nq_pairs = (nq + 255) / 256;
   // Every CTA streams the dictionary tiles in the same order at about the
   // same pace, so L2 serves nearly all of them whatever the dictionary size.
-  // A split restarts every query's best list (about MC*ln(N/MC) insertions
-  // each), so the dictionary is split only as far as needed to give every SM
-  // (query pair, split) items.
-  int64_t nsplit = nsplit_override > 0 ? nsplit_override : (2ll * d->ctx->n_sm + nq_pairs - 1) / nq_pairs;
+  // The persistent CTAs take (query pair, split) items in turn, so the last
+  // round decides the run time: the split count minimises the tiles of the
+  // busiest CTA, each item charged a restart of its best lists (about
+  // MC*ln(N/MC) insertions per query, spread over the whole split as warp-
+  // divergent appends), measured at about kRestartTiles dictionary tiles.
+  constexpr int64_t kRestartTiles = 2048;
+  int64_t nsplit = nsplit_override;
+  if (nsplit <= 0) {
+    int64_t best_cost = INT64_MAX;
+    const int64_t grid = std::max(1, d->ctx->n_sm);
+    for (int64_t ns = 1; ns <= std::min<int64_t>(8, nd_tiles); ++ns) {
+      const int64_t tps = (nd_tiles + ns - 1) / ns;
+      if ((ns - 1) * tps >= nd_tiles) continue;   // the last split would be empty
+      const int64_t rounds = (nq_pairs * ns + grid - 1) / grid;
+      const int64_t cost = rounds * (tps + kRestartTiles);
+      if (cost < best_cost) {
+        best_cost = cost;
+        nsplit = ns;
+      }
+    }
+  }
   p.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
   p.q_rows = tc_rows_padded(nq, true);
   p.KCH = p.prec == 0 ? 80 : 32;
