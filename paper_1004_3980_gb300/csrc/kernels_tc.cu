@@ -27,7 +27,11 @@
 
 namespace {
 
-constexpr int TC_THREADS = 320;   // warp 0 producer, warp 1 MMA, warps 2..9 epilogue
+// warp 0 producer, warps 1 and 10 MMA issue (query tile 0 and 1), warps 2..9
+// epilogue.  One thread issuing every MMA, wait and commit of a dictionary
+// tile was measured to bound the kernel (about 60 cycles per issued MMA), so
+// the two query tiles have an issuing thread each.
+constexpr int TC_THREADS = 352;
 // Dictionary-tile ring depth: enough bulk copies in flight to cover their
 // latency, within the shared memory left by the query tiles and the buffers.
 __host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 5 : 16; }
@@ -166,6 +170,38 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32]) 
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// As tmem_ld32_issue, and `m` receives the minimum of the 32 values, reduced
+// in the TMEM load path (tcgen05.ld.red, sm_103a): the per-column threshold
+// test of the scan then costs one comparison instead of a min tree on the
+// 16-lane ALU pipe.
+__device__ __forceinline__ void tmem_ld32_min_issue(uint32_t taddr, float (&v)[32], float& m) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=f"(m)
+      : "r"(taddr)
+      : "memory");
+}
+// Waits for the TMEM loads in flight; `v` and `m` (the destinations of the
+// last one) are in-out operands, so the compiler reads those registers only
+// after the wait and may do other work between the load and the wait.
+__device__ __forceinline__ void tmem_ld_wait(float (&v)[32], float& m) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                 "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                 "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+f"(m)
+               :
+               : "memory");
+}
 
 // 32 consecutive TMEM columns of this warp's 32 lanes (one lane per thread).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -276,25 +312,15 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 __device__ __forceinline__ float min8(const float (&v)[32], int o) {
   return fmin3(fmin3(v[o], v[o + 1], v[o + 2]), fmin3(v[o + 3], v[o + 4], v[o + 5]), fminf(v[o + 6], v[o + 7]));
 }
-// Minimum of the 32 values (16 instructions).
-__device__ __forceinline__ float min32(const float (&v)[32]) {
-  float a[11];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) a[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-  a[10] = fminf(v[30], v[31]);
-  const float b0 = fmin3(a[0], a[1], a[2]), b1 = fmin3(a[3], a[4], a[5]);
-  const float b2 = fmin3(a[6], a[7], a[8]);
-  return fmin3(fmin3(b0, b1, b2), a[9], a[10]);
-}
 
-// One 32-column chunk of a query's accumulator row: the chunk minimum is
-// compared with the list threshold; columns below it are appended.
+// One 32-column chunk of a query's accumulator row (`m`: its minimum, from
+// the load): compared with the list threshold; columns below it are appended.
 template <int MC>
-__device__ __forceinline__ void scan_chunk(const float (&v)[32], int col0, float (&ld)[MC], int (&li)[MC],
-                                           float& thr, float* bv, int* bi, int& cnt) {
+__device__ __forceinline__ void scan_chunk(const float (&v)[32], float m, int col0, float (&ld)[MC],
+                                           int (&li)[MC], float& thr, float* bv, int* bi, int& cnt) {
   // room for the up to 32 appends of this chunk in every lane
   if (__any_sync(0xffffffffu, cnt > kBuf - 32)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
-  if (min32(v) < thr) {
+  if (m < thr) {
     // rare: append the columns below the (possibly stale) threshold to this
     // lane's buffer; they are merged into the list later, by the whole warp
 #pragma unroll
@@ -348,17 +374,17 @@ __device__ __forceinline__ void coop_insert(float& e, int& ei, float x, int id, 
 }
 
 // One 32-column chunk of the warp's 32 query rows (lane L holds row L's
-// values v[0..31]): for each lane whose chunk minimum is below its
-// threshold, the warp visits that lane's groups of 8 columns holding values
-// below the threshold and inserts them.
+// values v[0..31], their minimum `m` from the load): for each lane whose
+// chunk minimum is below its threshold, the warp visits that lane's groups
+// of 8 columns holding values below the threshold and inserts them.
 template <int MC>
-__device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], int col0, float* rows_d, int* rows_i,
-                                                float& thr, int lane) {
+__device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], float m, int col0, float* rows_d,
+                                                int* rows_i, float& thr, int lane) {
+  unsigned hit = __ballot_sync(kFull, m < thr);
+  if (!hit) return;
   float gm[4];
 #pragma unroll
   for (int g = 0; g < 4; ++g) gm[g] = min8(v, g * 8);
-  const float m = fmin3(gm[0], gm[1], fminf(gm[2], gm[3]));
-  unsigned hit = __ballot_sync(kFull, m < thr);
   while (hit) {                                 // warp-uniform from here on
     const int L = __ffs(hit) - 1;
     hit &= hit - 1;
@@ -397,8 +423,8 @@ __device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], int col0, 
 }
 
 template <int KC, int MC, uint32_t AB_TYPE>
-// Ten warps sit 3/3/2/2 on the four SM sub-partitions (16K registers each),
-// which caps a thread at 168 registers.
+// Eleven warps sit 3/3/3/2 on the four SM sub-partitions (16K registers
+// each), which caps a thread at 168 registers.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
   constexpr int kKSteps = KC / 2;                     // MMA K = 16 = two 8-element chunks
@@ -413,9 +439,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   uint64_t* a_empty = bars + 1;
   uint64_t* b_full = bars + 2;                 // [kStages]
   uint64_t* b_empty = b_full + kStages;        // [kStages]
-  uint64_t* acc_full = b_empty + kStages;      // [2]
-  uint64_t* acc_empty = acc_full + 2;          // [2]
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+  // accumulator hand-off per (buffer, query tile): a query tile's 128
+  // columns go back to the MMA as soon as its 4 epilogue warps have read them
+  uint64_t* acc_full = b_empty + kStages;      // [2][2]
+  uint64_t* acc_empty = acc_full + 4;          // [2][2]
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBuf][256]
   int* buf_i = (int*)(buf_v + kBuf * 256);               // [kBuf][256]
@@ -423,14 +451,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
-    mbar_init(a_empty, 1);
+    mbar_init(a_empty, 2);    // one commit per MMA thread
     for (int s = 0; s < kStages; ++s) {
       mbar_init(b_full + s, 1);
-      mbar_init(b_empty + s, 1);
+      mbar_init(b_empty + s, 2);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 4; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, 256);
+      mbar_init(acc_empty + b, 128);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -475,17 +503,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issue (one thread) ----------------
+  } else if (warp == 1 || warp == 10) {
+    // ---------------- MMA issue: one thread per query tile ----------------
     if (lane == 0) {
+      const int qt = warp == 1 ? 0 : 1;
       int stage = 0, buf = 0, items = 0;
       uint32_t phase = 0, a_phase = 0;
       uint32_t accp[2] = {0u, 0u};
-      // Descriptors of the first K step of both query tiles and of ring
+      // Descriptors of the first K step of this query tile and of ring
       // stage 0; a K step adds 2 core-matrix columns (4 KiB), a stage one tile
       // (start address field in 16-byte units; every address stays below
       // 256 KiB, so the 14-bit field never carries).
-      const uint64_t ad0 = smem_desc(smem_u32(sA), TC_ROWS * 16, 128);
+      const uint64_t ad0 = smem_desc(smem_u32(sA + qt * kTileBytes), TC_ROWS * 16, 128);
       const uint64_t bd0 = smem_desc(smem_u32(sB), TC_ROWS * 16, 128);
       constexpr uint64_t kKStepAdv = (2 * TC_ROWS * 16) >> 4;
       constexpr uint64_t kTileAdv = kTileBytes >> 4;
@@ -499,22 +528,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
           if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status) ||
-              !mbar_wait_fast(acc_empty + buf, accp[buf] ^ 1u, abort_flag, a.status)) {
+              !mbar_wait_fast(acc_empty + buf * 2 + qt, accp[buf] ^ 1u, abort_flag, a.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint64_t bd_s = bd0 + (uint64_t)stage * kTileAdv;
+          const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
 #pragma unroll
-          for (int qt = 0; qt < 2; ++qt) {
-            const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
-#pragma unroll
-            for (int ks = 0; ks < kKSteps; ++ks)
-              mma_f16(d_addr, ad0 + (uint64_t)qt * kTileAdv + ks * kKStepAdv, bd_s + ks * kKStepAdv, kIdesc,
-                      ks > 0 ? 1u : 0u);
-          }
-          mma_commit(b_empty + stage);
-          mma_commit(acc_full + buf);
+          for (int ks = 0; ks < kKSteps; ++ks)
+            mma_f16(d_addr, ad0 + ks * kKStepAdv, bd_s + ks * kKStepAdv, kIdesc, ks > 0 ? 1u : 0u);
+          mma_commit(acc_full + buf * 2 + qt);   // also frees the ring stage (epilogue)
           accp[buf] ^= 1u;
           buf ^= 1;
           if (++stage == kStages) {
@@ -541,6 +565,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
     int* bi = buf_i + ew * 32 + lane;
     int buf = 0;
     uint32_t accp[2] = {0u, 0u};
+    // The accumulator of a (tile, query tile) being complete means its MMAs
+    // have read their ring stage: one lane per query tile releases the stage
+    // (two arrivals free it), which keeps that commit off the MMA threads.
+    int stage = 0;
+    const bool releaser = (ew & 3) == 0 && lane == 0;
     if constexpr (MC > 16) {
       // cooperative lists: this warp's 32 lists [32][MC] in the buffer region
       float* rows_d = buf_v + ew * 32 * MC;
@@ -561,25 +590,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         float thr = FLT_MAX;
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
-          const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf, accp[buf], abort_flag, a.status));
+          const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
           if (!w) {
             ok = false;
             break;
           }
           tc_fence_after();
+          if (releaser) mbar_arrive(b_empty + stage);
+          if (++stage == kStages) stage = 0;
           const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
+          // the load of the next 32 columns is in flight while a chunk is scanned
+          float va[32], vb[32], ma, mb;
+          tmem_ld32_min_issue(tb, va, ma);
+          tmem_ld_wait(va, ma);
 #pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            float va[32], vb[32];
-            tmem_ld32_issue(tb + h * 64, va);
-            tmem_ld32_issue(tb + h * 64 + 32, vb);
-            tmem_ld_wait();
-            if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+          for (int c = 0; c < 4; c += 2) {
+            tmem_ld32_min_issue(tb + (c + 1) * 32, vb, mb);
+            scan_chunk_coop<MC>(va, ma, t * TC_ROWS + c * 32, rows_d, rows_i, thr, lane);
+            tmem_ld_wait(vb, mb);
+            if (c == 2) {   // every TMEM read of this tile is done: hand the buffer back
               tc_fence_before();
-              mbar_arrive(acc_empty + buf);
+              mbar_arrive(acc_empty + buf * 2 + qt);
+            } else {
+              tmem_ld32_min_issue(tb + (c + 2) * 32, va, ma);
             }
-            scan_chunk_coop<MC>(va, t * TC_ROWS + h * 64, rows_d, rows_i, thr, lane);
-            scan_chunk_coop<MC>(vb, t * TC_ROWS + h * 64 + 32, rows_d, rows_i, thr, lane);
+            scan_chunk_coop<MC>(vb, mb, t * TC_ROWS + (c + 1) * 32, rows_d, rows_i, thr, lane);
+            if (c == 0) tmem_ld_wait(va, ma);
           }
           accp[buf] ^= 1u;
           buf ^= 1;
@@ -621,40 +657,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
         // warp-collective TMEM loads
-        const bool w = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + buf, accp[buf], abort_flag, a.status));
+        const bool w = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
         if (!w) {
           ok = false;
           break;
         }
         tc_fence_after();
+        if (releaser) mbar_arrive(b_empty + stage);
+        if (++stage == kStages) stage = 0;
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
-        if constexpr (MC <= 16) {
+        {
+          // the load of the next 32 columns is in flight while a chunk is scanned
+          float va[32], vb[32], ma, mb;
+          tmem_ld32_min_issue(tb, va, ma);
+          tmem_ld_wait(va, ma);
 #pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            // two 32-column loads in flight per wait
-            float va[32], vb[32];
-            tmem_ld32_issue(tb + h * 64, va);
-            tmem_ld32_issue(tb + h * 64 + 32, vb);
-            tmem_ld_wait();
-            if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+          for (int c = 0; c < 4; c += 2) {
+            tmem_ld32_min_issue(tb + (c + 1) * 32, vb, mb);
+            scan_chunk<MC>(va, ma, t * TC_ROWS + c * 32, ld, li, thr, bv, bi, cnt);
+            tmem_ld_wait(vb, mb);
+            if (c == 2) {   // every TMEM read of this tile is done: hand the buffer back
               tc_fence_before();
-              mbar_arrive(acc_empty + buf);
+              mbar_arrive(acc_empty + buf * 2 + qt);
+            } else {
+              tmem_ld32_min_issue(tb + (c + 2) * 32, va, ma);
             }
-            scan_chunk<MC>(va, t * TC_ROWS + h * 64, ld, li, thr, bv, bi, cnt);
-            scan_chunk<MC>(vb, t * TC_ROWS + h * 64 + 32, ld, li, thr, bv, bi, cnt);
-          }
-        } else {
-          // the longer list leaves registers for one chunk at a time
-#pragma unroll 1
-          for (int c = 0; c < 4; ++c) {
-            float v[32];
-            tmem_ld32_issue(tb + c * 32, v);
-            tmem_ld_wait();
-            if (c == 3) {
-              tc_fence_before();
-              mbar_arrive(acc_empty + buf);
-            }
-            scan_chunk<MC>(v, t * TC_ROWS + c * 32, ld, li, thr, bv, bi, cnt);
+            scan_chunk<MC>(vb, mb, t * TC_ROWS + (c + 1) * 32, ld, li, thr, bv, bi, cnt);
+            if (c == 0) tmem_ld_wait(va, ma);
           }
         }
         accp[buf] ^= 1u;
