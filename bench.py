@@ -349,7 +349,7 @@ def run_single(a, wl, config, rank, world, local):
     if not a.no_extras:
         # BF16 form: same inputs; recall of its neighbours and PSNR of its
         # output against the exact form
-        p1 = params(precision=1, rerank_mult=4)
+        p1 = params(precision=1, rerank_mult=2)
         for _ in range(2):
             Z.upscale(ix, lr, p1, out=out)
         ms1 = timed_steps(lambda: Z.upscale(ix, lr, p1, out=out), a.steps, st, torch)
@@ -391,7 +391,7 @@ def run_batch(a, config, rank, world, local):
     lrs = [(s, torch.from_numpy(S.make_image(seed, h, w)).cuda()) for seed, h, w, s in shapes]
     hr_px = sum(s * s * x.shape[0] * x.shape[1] for s, x in lrs)
     nq = sum((x.shape[0] - 4) * (x.shape[1] - 4) for _, x in lrs)
-    p1 = Z.UpscaleParams(K=8, bp_iters=5, precision=1, rerank_mult=4)
+    p1 = Z.UpscaleParams(K=8, bp_iters=5, precision=1, rerank_mult=2)
     st = torch.cuda.current_stream()
     outs, _ = Z.upscale_batch(indexes, lrs, p1)            # autotune + record
     for _ in range(max(0, a.warmup - 1)):

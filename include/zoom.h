@@ -90,7 +90,9 @@ typedef struct {
  * iterations (0..64) with spatial sigma sigma_spatial (pixels), range sigma
  * sigma_range and window radius bp_radius (1..7) (Sec. 4.3).
  * precision: 0 = exact FP32 neighbour search; 1 = BF16 tensor-core distance
- * filter keeping the rerank_mult*K best, then FP32 exact rerank.
+ * filter keeping per query the best 16 (rerank_mult*K <= 16) or 32 chunks of
+ * 32 consecutive dictionary entries by their smallest BF16 distance, then the
+ * FP32 exact rerank of those chunks' entries.
  * fp64_cond_threshold: the LLE solve runs in FP64 for a query whose
  * condition bound (trace(G) + eps) / eps exceeds it.
  * search (precision 0 only): 0 = automatic, 1 = SIMT scan of the dictionary

@@ -4,9 +4,13 @@
 // of the dictionary, so the search is a dense (queries x dictionary)
 // contraction.  A tensor-core pass computes, for every (query, entry) pair,
 //   acc = ||c||^2 - 2 q.c        (d~ = ||q||^2 + acc approximates |q - c|^2)
-// and keeps per query the MC smallest d~ of every dictionary split.  A
-// rerank kernel then computes the exact FP32 difference-form distance of the
-// kept entries, tests LSH membership and selects the K nearest members.
+// and keeps per query, for every dictionary split, the MC 32-entry chunks
+// (consecutive entries) with the smallest minimum d~; the minimum of a chunk
+// comes with its TMEM load (tcgen05.ld.red), so the epilogue costs one
+// comparison per chunk.  Any entry of the top MC lies in one of those chunks.
+// A rerank kernel then computes the exact FP32 difference-form distance of
+// the entries of the listed chunks in ascending chunk order, tests LSH
+// membership and selects the K nearest members.
 //
 // Exact form (FP16, 3 terms): q = q_hi + q_lo, c = c_hi + c_lo (fp16 pairs),
 //   A row = [q_hi | q_lo | q_hi | 1 | 1 | 0 0 0]            (K = 80)
@@ -14,10 +18,11 @@
 // so acc misses only -2 q_lo.c_lo (about 2^-22 relative).  With an error
 // bound delta on |d~ - d|, a query whose K-th exact distance D_K satisfies
 // T - delta > D_K (T: smallest list threshold over the splits) provably has
-// every nearer member inside the lists; other queries are re-run by the
-// exact SIMT scan.  The result equals the exact scan's.
+// every nearer member inside the listed chunks; other queries are re-run by
+// the exact SIMT scan.  The result equals the exact scan's.
 // Precision form (BF16, 1 term): A = [q | 1 1 1 | 0..], B = [-2c | n1 n2 n3 | 0..]
-// (K = 32); the rerank takes the best rerank_mult*K of the merged lists.
+// (K = 32); the rerank examines the listed chunks until a BF16 error bound
+// rules the rest out, without the proof.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
@@ -34,7 +39,7 @@ namespace {
 constexpr int TC_THREADS = 352;
 // Dictionary-tile ring depth: enough bulk copies in flight to cover their
 // latency, within the shared memory left by the query tiles and the buffers.
-__host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 5 : 16; }
+__host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 7 : 16; }
 constexpr int kBarBytes = 512;
 constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
 constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
@@ -152,28 +157,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // Issues the load of 32 consecutive TMEM columns of this warp's 32 lanes
-// (one lane per thread); the registers are valid after tmem_ld_wait().
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32]) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(v);
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-// As tmem_ld32_issue, and `m` receives the minimum of the 32 values, reduced
-// in the TMEM load path (tcgen05.ld.red, sm_103a): the per-column threshold
-// test of the scan then costs one comparison instead of a min tree on the
-// 16-lane ALU pipe.
+// (one lane per thread) into `v`, and `m` receives the minimum of the 32
+// values, reduced in the TMEM load path (tcgen05.ld.red, sm_103a): the
+// threshold test of a chunk costs one comparison instead of a min tree on the
+// 16-lane ALU pipe.  The registers are valid after tmem_ld_wait.
 __device__ __forceinline__ void tmem_ld32_min_issue(uint32_t taddr, float (&v)[32], float& m) {
   uint32_t* r = reinterpret_cast<uint32_t*>(v);
   asm volatile(
@@ -203,23 +190,18 @@ __device__ __forceinline__ void tmem_ld_wait(float (&v)[32], float& m) {
                : "memory");
 }
 
-// 32 consecutive TMEM columns of this warp's 32 lanes (one lane per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+// After a tcgen05.wait::ld that covered the load into `v` and `m`: tells the
+// compiler those registers are valid from here on (no instruction).
+__device__ __forceinline__ void tmem_regs_ready(float (&v)[32], float& m) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                 "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                 "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                 "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+f"(m)
+               :
+               : "memory");
 }
 
 // Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
@@ -251,8 +233,8 @@ struct TcArgs {
   int nd_tiles;          // ceil(nd / 128)
   int nsplit;
   int tiles_per_split;
-  float* out_d;          // [nsplit][nq][MC] d~ ascending
-  int32_t* out_id;       // [nsplit][nq][MC]
+  float* out_d;          // [nsplit][nq][MC] chunk minimum d~, ascending (FLT_MAX: none)
+  int32_t* out_id;       // [nsplit][nq][MC] chunk index (entries 32c..32c+31; -1: none)
   unsigned int* status;
 };
 
@@ -280,18 +262,19 @@ __device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float 
   thr = ld[MC - 1];
 }
 
-// Per epilogue lane, columns below the threshold are first appended to a
-// shared-memory buffer of kBuf slots (a few instructions per column) and
-// merged into the sorted register list when some lane of the warp runs out
-// of room: the merge loop then runs for all lanes together, so the sorted
-// insertions execute with the warp converged.
-constexpr int kBuf = 40;
+// Per epilogue lane, chunks below the threshold are first appended to a
+// shared-memory buffer of kBuf slots (a few instructions each) and merged
+// into the sorted register list when some lane of the warp runs out of room:
+// the merge loop then runs for all lanes together, so the sorted insertions
+// execute with the warp converged.
+constexpr int kBuf = 16;
+constexpr unsigned kFull = 0xffffffffu;
 
 template <int MC>
 __device__ __forceinline__ void flush_appends(float (&ld)[MC], int (&li)[MC], float& thr,
                                               const float* bv, const int* bi, int& cnt) {
   const int n = cnt;
-  const int nmax = __reduce_max_sync(0xffffffffu, n);
+  const int nmax = __reduce_max_sync(kFull, n);
   for (int s = 0; s < nmax; ++s) {
     if (s < n) {
       const float x = bv[s * 256];
@@ -301,124 +284,13 @@ __device__ __forceinline__ void flush_appends(float (&ld)[MC], int (&li)[MC], fl
   cnt = 0;
 }
 
-// Three-input minimum (sm_100 family): halves the instructions of a
-// reduction.  The accumulator values are finite.
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
-  float d;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-  return d;
-}
-// Minimum of 8 consecutive values v[o..o+7].
-__device__ __forceinline__ float min8(const float (&v)[32], int o) {
-  return fmin3(fmin3(v[o], v[o + 1], v[o + 2]), fmin3(v[o + 3], v[o + 4], v[o + 5]), fminf(v[o + 6], v[o + 7]));
-}
-
-// One 32-column chunk of a query's accumulator row (`m`: its minimum, from
-// the load): compared with the list threshold; columns below it are appended.
-template <int MC>
-__device__ __forceinline__ void scan_chunk(const float (&v)[32], float m, int col0, float (&ld)[MC],
-                                           int (&li)[MC], float& thr, float* bv, int* bi, int& cnt) {
-  // room for the up to 32 appends of this chunk in every lane
-  if (__any_sync(0xffffffffu, cnt > kBuf - 32)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+// A 32-column chunk whose minimum `m` is below the list threshold is a
+// candidate: its index is appended (rare after the first tiles).
+__device__ __forceinline__ void chunk_test(float m, int chunk, float thr, float* bv, int* bi, int& cnt) {
   if (m < thr) {
-    // rare: append the columns below the (possibly stale) threshold to this
-    // lane's buffer; they are merged into the list later, by the whole warp
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      if (min8(v, g * 8) < thr) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float x = v[g * 8 + j];
-          if (x < thr) {
-            bv[cnt * 256] = x;
-            bi[cnt * 256] = col0 + g * 8 + j;
-            ++cnt;
-          }
-        }
-      }
-    }
-  }
-}
-
-// Warp-cooperative best lists (used for the longer lists, MC = 32).  Each
-// epilogue lane owns one query; the list of that query's MC smallest values
-// (ascending) lives in shared memory and is held one entry per lane while
-// the warp works on it.  A column below a query's threshold is inserted by
-// the whole warp at once: a ballot gives its rank, a lane shift makes room.
-constexpr unsigned kFull = 0xffffffffu;
-
-// w[j] for a run-time j in [0, 8) by a binary tree of selects (registers).
-__device__ __forceinline__ float select8(const float (&w)[8], int j) {
-  float c[4], d[2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? w[i + 4] : w[i];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) d[i] = (j & 2) ? c[i + 2] : c[i];
-  return (j & 1) ? d[1] : d[0];
-}
-
-template <int MC>
-__device__ __forceinline__ void coop_insert(float& e, int& ei, float x, int id, int lane) {
-  // e (lane j) = entry j of the list; lanes >= MC hold FLT_MAX
-  const int pos = __popc(__ballot_sync(kFull, e <= x));   // entries not above x
-  const float eu = __shfl_up_sync(kFull, e, 1);
-  const int iu = __shfl_up_sync(kFull, ei, 1);
-  if (lane > pos) {
-    e = eu;
-    ei = iu;
-  } else if (lane == pos) {
-    e = x;
-    ei = id;
-  }
-  if (lane >= MC) e = FLT_MAX;
-}
-
-// One 32-column chunk of the warp's 32 query rows (lane L holds row L's
-// values v[0..31], their minimum `m` from the load): for each lane whose
-// chunk minimum is below its threshold, the warp visits that lane's groups
-// of 8 columns holding values below the threshold and inserts them.
-template <int MC>
-__device__ __forceinline__ void scan_chunk_coop(const float (&v)[32], float m, int col0, float* rows_d,
-                                                int* rows_i, float& thr, int lane) {
-  unsigned hit = __ballot_sync(kFull, m < thr);
-  if (!hit) return;
-  float gm[4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) gm[g] = min8(v, g * 8);
-  while (hit) {                                 // warp-uniform from here on
-    const int L = __ffs(hit) - 1;
-    hit &= hit - 1;
-    float tL = __shfl_sync(kFull, thr, L);
-    float* rd = rows_d + L * MC;
-    int* ri = rows_i + L * MC;
-    float e = lane < MC ? rd[lane] : FLT_MAX;
-    int ei = lane < MC ? ri[lane] : -1;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      if (__shfl_sync(kFull, gm[g], L) < tL) {
-        float w8[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) w8[j] = v[g * 8 + j];
-        uint32_t msk = 0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) msk |= (w8[j] < tL ? 1u : 0u) << j;
-        msk = __shfl_sync(kFull, msk, L);      // lane L's columns below its threshold
-        while (msk) {
-          const int j = __ffs(msk) - 1;
-          msk &= msk - 1;
-          const float x = __shfl_sync(kFull, select8(w8, j), L);
-          if (x < tL) {
-            coop_insert<MC>(e, ei, x, col0 + g * 8 + j, lane);
-            tL = __shfl_sync(kFull, e, MC - 1);
-          }
-        }
-      }
-    }
-    if (lane < MC) {
-      rd[lane] = e;
-      ri[lane] = ei;
-    }
-    if (lane == L) thr = tL;
+    bv[cnt * 256] = m;
+    bi[cnt * 256] = chunk;
+    ++cnt;
   }
 }
 
@@ -555,7 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
       if (items > 0) mbar_wait(a_empty, (uint32_t)(items - 1) & 1u, abort_flag, a.status);
     }
   } else {
-    // ---------------- epilogue: per-query best lists ----------------
+    // ------------- epilogue: per query, the MC best 32-entry chunks -------------
     const int ew = warp - 2;            // 0..7
     const int qt = ew >> 2;             // query tile within the pair
     const int quad = warp & 3;          // TMEM lane quadrant this warp may access
@@ -570,74 +442,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
     // (two arrivals free it), which keeps that commit off the MMA threads.
     int stage = 0;
     const bool releaser = (ew & 3) == 0 && lane == 0;
-    if constexpr (MC > 16) {
-      // cooperative lists: this warp's 32 lists [32][MC] in the buffer region
-      float* rows_d = buf_v + ew * 32 * MC;
-      int* rows_i = (int*)(buf_v + 256 * MC) + ew * 32 * MC;
-      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
-        const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
-        const int t0 = split * a.tiles_per_split;
-        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
-        const int64_t q0 = ((int64_t)qp * 2 + qt) * TC_ROWS + quad * 32;   // lane 0's query
-        const float qn = q0 + lane < a.nq ? a.qn[q0 + lane] : 0.f;
-        for (int L = 0; L < 32; ++L)
-          if (lane < MC) {
-            rows_d[L * MC + lane] = FLT_MAX;
-            rows_i[L * MC + lane] = -1;
-          }
-        __syncwarp();
-        float thr = FLT_MAX;
-        bool ok = true;
-        for (int t = t0; t < t1; ++t) {
-          const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
-          if (!w) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          if (releaser) mbar_arrive(b_empty + stage);
-          if (++stage == kStages) stage = 0;
-          const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
-          // the load of the next 32 columns is in flight while a chunk is scanned
-          float va[32], vb[32], ma, mb;
-          tmem_ld32_min_issue(tb, va, ma);
-          tmem_ld_wait(va, ma);
-#pragma unroll 1
-          for (int c = 0; c < 4; c += 2) {
-            tmem_ld32_min_issue(tb + (c + 1) * 32, vb, mb);
-            scan_chunk_coop<MC>(va, ma, t * TC_ROWS + c * 32, rows_d, rows_i, thr, lane);
-            tmem_ld_wait(vb, mb);
-            if (c == 2) {   // every TMEM read of this tile is done: hand the buffer back
-              tc_fence_before();
-              mbar_arrive(acc_empty + buf * 2 + qt);
-            } else {
-              tmem_ld32_min_issue(tb + (c + 2) * 32, va, ma);
-            }
-            scan_chunk_coop<MC>(vb, mb, t * TC_ROWS + (c + 1) * 32, rows_d, rows_i, thr, lane);
-            if (c == 0) tmem_ld_wait(va, ma);
-          }
-          accp[buf] ^= 1u;
-          buf ^= 1;
-        }
-        if (!ok) break;
-        // write the 32 lists of this warp, one list per iteration (coalesced)
-        for (int L = 0; L < 32; ++L) {
-          const float qnL = __shfl_sync(kFull, qn, L);
-          const int64_t qL = q0 + L;
-          if (qL < a.nq && lane < MC) {
-            const float dv = rows_d[L * MC + lane];
-            const int iv = rows_i[L * MC + lane];
-            const bool real = iv >= 0 && iv < a.nd;
-            a.out_d[((int64_t)split * a.nq + qL) * MC + lane] = real ? qnL + dv : FLT_MAX;
-            a.out_id[((int64_t)split * a.nq + qL) * MC + lane] = real ? iv : -1;
-          }
-        }
-        __syncwarp();
-      }
-    } else
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;   // warp-uniform exit
+      if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
       const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
       const int t0 = split * a.tiles_per_split;
       const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
@@ -657,7 +463,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
         // warp-collective TMEM loads
-        const bool w = __all_sync(0xffffffffu, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
+        const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
         if (!w) {
           ok = false;
           break;
@@ -665,26 +471,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         tc_fence_after();
         if (releaser) mbar_arrive(b_empty + stage);
         if (++stage == kStages) stage = 0;
+        // room for this tile's up to 4 appends in every lane
+        if (__any_sync(kFull, cnt > kBuf - 4)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
-        {
-          // the load of the next 32 columns is in flight while a chunk is scanned
-          float va[32], vb[32], ma, mb;
-          tmem_ld32_min_issue(tb, va, ma);
-          tmem_ld_wait(va, ma);
+        // only the chunk minima are used (the loaded values are dead)
 #pragma unroll 1
-          for (int c = 0; c < 4; c += 2) {
-            tmem_ld32_min_issue(tb + (c + 1) * 32, vb, mb);
-            scan_chunk<MC>(va, ma, t * TC_ROWS + c * 32, ld, li, thr, bv, bi, cnt);
-            tmem_ld_wait(vb, mb);
-            if (c == 2) {   // every TMEM read of this tile is done: hand the buffer back
-              tc_fence_before();
-              mbar_arrive(acc_empty + buf * 2 + qt);
-            } else {
-              tmem_ld32_min_issue(tb + (c + 2) * 32, va, ma);
-            }
-            scan_chunk<MC>(vb, mb, t * TC_ROWS + (c + 1) * 32, ld, li, thr, bv, bi, cnt);
-            if (c == 0) tmem_ld_wait(va, ma);
+        for (int h = 0; h < 2; ++h) {
+          float va[32], vb[32], ma, mb;
+          tmem_ld32_min_issue(tb + h * 64, va, ma);
+          tmem_ld32_min_issue(tb + h * 64 + 32, vb, mb);
+          tmem_ld_wait(va, ma);
+          tmem_regs_ready(vb, mb);
+          if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+            tc_fence_before();
+            mbar_arrive(acc_empty + buf * 2 + qt);
           }
+          chunk_test(ma, t * 4 + 2 * h, thr, bv, bi, cnt);
+          chunk_test(mb, t * 4 + 2 * h + 1, thr, bv, bi, cnt);
         }
         accp[buf] ^= 1u;
         buf ^= 1;
@@ -696,7 +499,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
 #pragma unroll
         for (int j = 0; j < MC; ++j) {
-          const bool real = li[j] >= 0 && li[j] < a.nd;
+          const bool real = li[j] >= 0 && (int64_t)li[j] * 32 < a.nd;
           od[j] = real ? qn + ld[j] : FLT_MAX;
           oi[j] = real ? li[j] : -1;
         }
@@ -823,137 +626,155 @@ __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// rerank: exact FP32 distances of the listed entries in ascending d~ order,
-// LSH membership, K nearest members; exactness proof or fallback flag.
+// rerank: one warp per query.  Chunks are taken in ascending order of their
+// filter minimum over the split lists; the 32 entries of a chunk are examined
+// by the 32 lanes (exact FP32 distance in difference form, LSH membership for
+// the entries that could still enter the K best).  It stops once no entry of
+// a further chunk can beat the K-th member: every entry of a chunk has
+// d >= chunk minimum - delta, delta bounding |d~ - d| for any entry that
+// could.  Exact form: the unlisted chunks have d~ >= T (smallest list
+// threshold over the splits), so T - delta > D_K proves the result; a query
+// it cannot settle is flagged for the SIMT re-run.
 // ---------------------------------------------------------------------------
-template <int D, int MC, int KMAX>
-__global__ __launch_bounds__(128) void k_rerank(
+template <int D, int MC>
+__global__ __launch_bounds__(256) void k_rerank(
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
     const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
-    const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ ld,
-    const int32_t* __restrict__ li, int nsplit, int K, int exact, int max_examine, float eps_rel,
+    const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
+    const int32_t* __restrict__ lc, int nsplit, int K, int exact, float c_qr, float c_sq,
     int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ fb_list,
     unsigned long long* __restrict__ counters) {
-  constexpr int SMAX = 8;
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nq) return;
+  constexpr int kDP = (D + 3) / 4 * 4;   // feature row stride (floats)
+  __shared__ float4 s_rows[8][32 * kDP / 4];
+  const int lane = threadIdx.x & 31;
+  float4* srow = s_rows[threadIdx.x >> 5];
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= nq) return;   // warp-uniform
   float qv[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) qv[i] = qfeat[q * dpad + i];
   const float qn = qn_arr[q];
-  // merge heads of the per-split lists (each ascending in d~)
-  int head[SMAX];
-  float T = FLT_MAX;
-#pragma unroll
-  for (int s = 0; s < SMAX; ++s) {
-    head[s] = 0;
-    if (s < nsplit) T = fminf(T, ld[((int64_t)s * nq + q) * MC + MC - 1]);
-  }
-  float bd[KMAX];
-  int bi[KMAX];
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    bd[j] = FLT_MAX;
-    bi[j] = INT_MAX;
-  }
-  int members = 0, examined = 0;
-  float delta = 0.f, dK = FLT_MAX;
   const float qnorm = sqrtf(qn);
-  bool flagged = false;
+  // lane s < nsplit follows the list of split s
+  const bool lister = lane < nsplit;
+  const int64_t lbase = ((int64_t)(lister ? lane : 0) * nq + q) * MC;
+  int head = 0;
+  float hv = lister ? lm[lbase] : FLT_MAX;
+  float T = lister ? lm[lbase + MC - 1] : FLT_MAX;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) T = fminf(T, __shfl_xor_sync(kFull, T, off));
+  // the K best members so far, ascending by (distance, ID): lane j < K holds rank j
+  float bd = FLT_MAX;
+  int bi = INT_MAX;
+  float dK = FLT_MAX, delta = 0.f;
+  int iK = INT_MAX, members = 0;
   while (true) {
-    // next entry in ascending d~ over the splits
-    float best = FLT_MAX;
-    int bs = -1;
+    // the listed chunk with the smallest minimum (ties: lower split)
+    float best = hv;
+    int bs = lane;
 #pragma unroll
-    for (int s = 0; s < SMAX; ++s) {
-      if (s < nsplit && head[s] < MC) {
-        const float v = ld[((int64_t)s * nq + q) * MC + head[s]];
-        if (v < best) {
-          best = v;
-          bs = s;
+    for (int off = 16; off; off >>= 1) {
+      const float ov = __shfl_xor_sync(kFull, best, off);
+      const int os = __shfl_xor_sync(kFull, bs, off);
+      if (ov < best || (ov == best && os < bs)) {
+        best = ov;
+        bs = os;
+      }
+    }
+    if (best == FLT_MAX) break;
+    if (members >= K && best - delta > dK) break;
+    const int chunk = __shfl_sync(kFull, lane == bs ? lc[lbase + head] : 0, bs);
+    if (lane == bs) {
+      ++head;
+      hv = head < MC ? lm[lbase + head] : FLT_MAX;
+    }
+    const int64_t e0 = (int64_t)chunk * 32;
+    const int64_t e = e0 + lane;
+    // the chunk's 32 feature rows are contiguous: staged through shared
+    // memory with 16-byte loads, then each lane reads its own row
+    const int nrows = chunk < 0 ? 0 : (nd - e0 < 32 ? (int)(nd - e0) : 32);
+    const float4* g = reinterpret_cast<const float4*>(dfeat + e0 * kDP);
+    __syncwarp();   // the previous chunk's rows have been read
+    for (int f = lane; f < nrows * (kDP / 4); f += 32) srow[f] = g[f];
+    __syncwarp();
+    float dd = FLT_MAX;
+    if (lane < nrows) {
+      float x[kDP];
+#pragma unroll
+      for (int k = 0; k < kDP / 4; ++k) {
+        const float4 v4 = srow[lane * (kDP / 4) + k];
+        x[4 * k] = v4.x;
+        x[4 * k + 1] = v4.y;
+        x[4 * k + 2] = v4.z;
+        x[4 * k + 3] = v4.w;
+      }
+      dd = 0.f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const float df = qv[i] - x[i];
+        dd = fmaf(df, df, dd);
+      }
+    }
+    // entries that could still enter the K best: LSH membership
+    bool mem = false;
+    if (dd != FLT_MAX && (members < K || dd < dK || (dd == dK && (int)e < iK))) {
+      int hits = 0;
+      for (int l = 0; l < L; ++l) hits += (qkeys[q * L + l] == dkeys[e * L + l]) ? 1 : 0;
+      mem = hits >= tmin;
+    }
+    unsigned mm = __ballot_sync(kFull, mem);
+    members += __popc(mm);
+    // insert the members in ascending (distance, ID) order
+    while (mm) {
+      const bool mine = (mm >> lane) & 1u;
+      float v = mine ? dd : FLT_MAX;
+      int id = mine ? (int)e : INT_MAX;
+      int src = lane;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, v, off);
+        const int oi = __shfl_xor_sync(kFull, id, off);
+        const int osr = __shfl_xor_sync(kFull, src, off);
+        if (ov < v || (ov == v && oi < id)) {
+          v = ov;
+          id = oi;
+          src = osr;
         }
       }
-    }
-    if (bs < 0 || best == FLT_MAX) break;
-    if (exact) {
-      // stop once no further listed entry can beat the K-th exact distance
-      if (members >= K && best - delta > dK) break;
-    } else if (examined >= max_examine) {
-      break;
-    }
-    const int id = li[((int64_t)bs * nq + q) * MC + head[bs]];
-    ++head[bs];
-    ++examined;
-    if (id < 0 || id >= nd) continue;
-    int hits = 0;
-    for (int l = 0; l < L; ++l) hits += (qkeys[q * L + l] == dkeys[(int64_t)id * L + l]) ? 1 : 0;
-    if (hits < tmin) continue;
-    float dd = 0.f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const float df = qv[i] - dfeat[(int64_t)id * dpad + i];
-      dd = fmaf(df, df, dd);
-    }
-    ++members;
-    // insert (dd, id) into the sorted top-K
-    float wd = bd[0];
-    int wi = bi[0];
-#pragma unroll
-    for (int j = 1; j < KMAX; ++j)
-      if (j == K - 1) {
-        wd = bd[j];
-        wi = bi[j];
-      }
-    if (dd < wd || (dd == wd && id < wi)) {
-      bool done = false;
-#pragma unroll
-      for (int j = KMAX - 1; j > 0; --j) {
-        if (j < K && !done) {
-          if (dd < bd[j - 1] || (dd == bd[j - 1] && id < bi[j - 1])) {
-            bd[j] = bd[j - 1];
-            bi[j] = bi[j - 1];
-          } else {
-            bd[j] = dd;
-            bi[j] = id;
-            done = true;
-          }
-        }
-      }
-      if (!done) {
-        bd[0] = dd;
-        bi[0] = id;
+      mm &= ~(1u << src);
+      const bool before = lane < K && (bd < v || (bd == v && bi < id));
+      const int pos = __popc(__ballot_sync(kFull, before));
+      if (pos >= K) break;   // the rest are larger still
+      const float ud = __shfl_up_sync(kFull, bd, 1);
+      const int ui = __shfl_up_sync(kFull, bi, 1);
+      if (lane == pos) {
+        bd = v;
+        bi = id;
+      } else if (lane > pos && lane < K) {
+        bd = ud;
+        bi = ui;
       }
     }
     if (members >= K) {
-      dK = bd[0];
-#pragma unroll
-      for (int j = 1; j < KMAX; ++j)
-        if (j == K - 1) dK = bd[j];
-    }
-    if (exact && members >= K) {
-      // |d~ - d| bound for any entry that could beat dK: such an entry has
-      // ||c|| <= ||q|| + sqrt(dK); the bound covers the FP16 split, the
-      // tensor-core FP32 accumulation and the FP32 rerank arithmetic.
+      dK = __shfl_sync(kFull, bd, K - 1);
+      iK = __shfl_sync(kFull, bi, K - 1);
+      // an entry that could beat dK has ||c|| <= ||q|| + sqrt(dK)
       const float rc = qnorm + sqrtf(dK) * 1.001f + 1e-6f;
-      delta = eps_rel * (6.f * qnorm * rc + rc * rc + qn) + 4e-6f * dK + 1e-12f;
+      delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + 4e-6f * dK + 1e-12f;
     }
   }
-  if (members < K) {
-    flagged = true;
-  } else if (exact) {
-    if (!(T - delta > dK)) flagged = true;
-  }
+  const bool flagged = members < K || (exact && !(T - delta > dK));
   if (flagged) {
-    const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
-    fb_list[slot] = (int32_t)q;
+    if (lane == 0) {
+      const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
+      fb_list[slot] = (int32_t)q;
+    }
     return;
   }
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j)
-    if (j < K) {
-      nbr[q * K + j] = bi[j];
-      dist[q * K + j] = bd[j];
-    }
+  if (lane < K) {
+    nbr[q * K + lane] = bi;
+    dist[q * K + lane] = bd;
+  }
 }
 
 }  // namespace
@@ -1038,31 +859,33 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
 template <int D, int MC>
 static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn, const uint64_t* qkeys,
                             int64_t nq, const float* dfeat, const uint64_t* dkeys, int64_t nd, int L,
-                            int tmin, const float* ld, const int32_t* li, int nsplit, int exact,
-                            int max_examine, float eps, int32_t* nbr, float* dist, int32_t* fb,
+                            int tmin, const float* ld, const int32_t* li, int nsplit, int exact, float c_qr,
+                            float c_sq, int32_t* nbr, float* dist, int32_t* fb,
                             unsigned long long* counters, cudaStream_t st) {
-  const int blocks = (int)((nq + 127) / 128);
-  if (K <= 8)
-    k_rerank<D, MC, 8><<<blocks, 128, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
-                                               li, nsplit, K, exact, max_examine, eps, nbr, dist, fb,
-                                               counters);
-  else
-    k_rerank<D, MC, 16><<<blocks, 128, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin,
-                                                ld, li, nsplit, K, exact, max_examine, eps, nbr, dist,
-                                                fb, counters);
+  const int64_t blocks = (nq + 7) / 8;   // one warp per query
+  k_rerank<D, MC><<<(unsigned)blocks, 256, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
+                                                    li, nsplit, K, exact, c_qr, c_sq, nbr, dist, fb, counters);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int exact, int max_examine, int32_t* nbr, float* dist, int32_t* fb,
-                          unsigned long long* counters, cudaStream_t st) {
-  const float eps = 1.0f / 65536.0f;
-  if (nsplit > 8) return cudaErrorInvalidValue;
+                          int exact, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
+                          cudaStream_t st) {
+  if (nsplit > 8 || K < 1 || K > 16 || dpad != (d + 3) / 4 * 4) return cudaErrorInvalidValue;
+  if (nq == 0) return cudaSuccess;
+  // |d~ - d| <= c_qr ||q|| r + c_sq (r^2 + ||q||^2) + 4e-6 d for an entry with
+  // ||c|| <= r.  Exact form: FP16 hi/lo split (the dropped q_lo.c_lo term and
+  // the rounding of the split, within 6 * 2^-16 ||q|| r), FP32 accumulation
+  // of 80 terms and the FP32 rerank (2^-16 (r^2 + ||q||^2), 4e-6 d).  BF16
+  // form: each operand rounded to 8 significant bits (2 * 2^-8 ||q|| r for
+  // the product term), 32 FP32 accumulations; used only to stop examining.
+  const float c_qr = exact ? 6.f / 65536.f : 1.05f / 128.f;
+  const float c_sq = exact ? 1.f / 65536.f : 1.f / 262144.f;
 #define ZOOM_RR(DD, MM)                                                                          \
   return rerank_k<DD, MM>(K, qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld, li, nsplit, \
-                          exact, max_examine, eps, nbr, dist, fb, counters, st)
+                          exact, c_qr, c_sq, nbr, dist, fb, counters, st)
   if (d == 25 && MC == 16) ZOOM_RR(25, 16);
   if (d == 25 && MC == 32) ZOOM_RR(25, 32);
   if (d == 9 && MC == 16) ZOOM_RR(9, 16);

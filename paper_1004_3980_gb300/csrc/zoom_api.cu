@@ -528,8 +528,8 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
-                      ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : 0, prm->rerank_mult * K, b.nbr,
-                      b.dist, fb, ctx->d_counters, st);
+                      ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : 0, b.nbr, b.dist, fb, ctx->d_counters,
+                      st);
   if (e == cudaSuccess)
     e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
                          ctx->d_counters + CNT_FALLBACK, st);

@@ -126,11 +126,14 @@ int tc_list_size(int precision, int K, int rerank_mult);
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
                           int64_t nd, int precision, int MC, int nsplit, int grid, float* out_d,
                           int32_t* out_id, unsigned int* status, cudaStream_t st);
+// ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
+// chunk index), ascending; exact = 1 for the FP16-split filter (proof and
+// fallback flags), 0 for the BF16 filter.
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int exact, int max_examine, int32_t* nbr, float* dist, int32_t* fb,
-                          unsigned long long* counters, cudaStream_t st);
+                          int exact, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
+                          cudaStream_t st);
 
 // backward / adjoint steps (kernels_backward.cu) and the key sort (kernels_build.cu)
 cudaError_t sort_keys_csr(const int32_t* keys32, int64_t n, int32_t* sorted_pos, uint64_t* ukeys,

@@ -61,7 +61,7 @@ class UpscaleParams:
     sigma_range: float = 0.1
     bp_radius: int = 3
     precision: int = 0
-    rerank_mult: int = 4
+    rerank_mult: int = 2
     fp64_cond_threshold: float = 1e6
     search: int = 0
 

@@ -74,17 +74,20 @@ def test_tc_exact_with_t_of_L(small):
     assert (a["nbr"] == b["nbr"]).all() and (a["dist"] == b["dist"]).all()
 
 
-def test_bf16_precision_form_recall_and_psnr(small):
+@pytest.mark.parametrize("rerank_mult", [2, 4])
+def test_bf16_precision_form_recall_and_psnr(small, rerank_mult):
+    """16- and 32-chunk lists of the BF16 filter (rerank_mult * K <= 16 or 32)."""
     case, ctx, d, ix = small
     wl = case.wl
     import paper_1004_3980_gb300 as Z
     ex = _query(ix, case.lr, wl, search=1)
-    pr = _query(ix, case.lr, wl, precision=1, rerank_mult=4)
+    pr = _query(ix, case.lr, wl, precision=1, rerank_mult=rerank_mult)
     K = wl.K
     rec = np.mean([len(set(pr["nbr"][q]) & set(ex["nbr"][q])) / K for q in range(len(ex["nbr"]))])
     assert rec >= 0.99, rec
     # PSNR of the precision form's HR output against the FP64 oracle
-    hr = Z.upscale(ix, torch.from_numpy(case.lr).cuda(), G.params(wl, precision=1)).cpu().numpy()
+    hr = Z.upscale(ix, torch.from_numpy(case.lr).cuda(),
+                   G.params(wl, precision=1, rerank_mult=rerank_mult)).cpu().numpy()
     x, _, _ = O.upscale(case.lr, case.odict, case.oindex, K, wl.reg_rel, wl.bp_iters, wl.blur_sigma,
                         wl.sigma_spatial, wl.sigma_range, wl.bp_radius)
     mse = float(np.mean((hr - x) ** 2))
