@@ -238,28 +238,22 @@ struct TcArgs {
   unsigned int* status;
 };
 
+// Inserts (v, id) into the ascending list, dropping its last entry; nothing
+// changes when v >= ld[MC-1].  Selects only, no branches: the lanes of a
+// warp insert at different positions without diverging (a branchy insertion
+// serialised those paths and cost ~1000 cycles per merged entry).
 template <int MC>
-__device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float v, int id, float& thr) {
-  // v < ld[MC-1]: insert keeping ascending order
-  bool done = false;
+__device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float v, int id) {
 #pragma unroll
   for (int j = MC - 1; j > 0; --j) {
-    if (!done) {
-      if (v < ld[j - 1]) {
-        ld[j] = ld[j - 1];
-        li[j] = li[j - 1];
-      } else {
-        ld[j] = v;
-        li[j] = id;
-        done = true;
-      }
-    }
+    const bool shift = v < ld[j - 1];
+    const bool here = v < ld[j];
+    ld[j] = shift ? ld[j - 1] : (here ? v : ld[j]);
+    li[j] = shift ? li[j - 1] : (here ? id : li[j]);
   }
-  if (!done) {
-    ld[0] = v;
-    li[0] = id;
-  }
-  thr = ld[MC - 1];
+  const bool first = v < ld[0];
+  ld[0] = first ? v : ld[0];
+  li[0] = first ? id : li[0];
 }
 
 // Per epilogue lane, chunks below the threshold are first appended to a
@@ -276,11 +270,12 @@ __device__ __forceinline__ void flush_appends(float (&ld)[MC], int (&li)[MC], fl
   const int n = cnt;
   const int nmax = __reduce_max_sync(kFull, n);
   for (int s = 0; s < nmax; ++s) {
-    if (s < n) {
-      const float x = bv[s * 256];
-      if (x < thr) list_push<MC>(ld, li, x, bi[s * 256], thr);
-    }
+    const bool has = s < n;
+    const float x = has ? bv[s * 256] : FLT_MAX;
+    const int xi = has ? bi[s * 256] : -1;
+    list_push<MC>(ld, li, x, xi);
   }
+  thr = ld[MC - 1];
   cnt = 0;
 }
 
@@ -471,8 +466,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         tc_fence_after();
         if (releaser) mbar_arrive(b_empty + stage);
         if (++stage == kStages) stage = 0;
-        // room for this tile's up to 4 appends in every lane
-        if (__any_sync(kFull, cnt > kBuf - 4)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
         // only the chunk minima are used (the loaded values are dead)
 #pragma unroll 1
@@ -491,6 +484,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         }
         accp[buf] ^= 1u;
         buf ^= 1;
+        // room for the next tile's up to 4 appends in every lane; merging
+        // here, with the accumulator already handed back, keeps the merge off
+        // the MMA's path
+        if (__any_sync(kFull, cnt > kBuf - 4)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
       }
       if (!ok) break;
       flush_appends<MC>(ld, li, thr, bv, bi, cnt);
