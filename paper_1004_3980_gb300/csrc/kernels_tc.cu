@@ -633,6 +633,52 @@ __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t
 // threshold over the splits), so T - delta > D_K proves the result; a query
 // it cannot settle is flagged for the SIMT re-run.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool lex_less(float a, int ai, float b, int bi) {
+  return a < b || (a == b && ai < bi);
+}
+
+// Bitonic sort of one (value, ID) pair per lane, ascending across the lanes.
+__device__ __forceinline__ void warp_sort32(float& v, int& id, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const float ov = __shfl_xor_sync(kFull, v, j);
+      const int oi = __shfl_xor_sync(kFull, id, j);
+      const bool keep_small = ((lane & j) == 0) == ((lane & k) == 0);
+      if (keep_small == lex_less(ov, oi, v, id)) {
+        v = ov;
+        id = oi;
+      }
+    }
+  }
+}
+
+// Merges 32 ascending candidates (one per lane) into the ascending K best
+// held by lanes 0..K-1: min(A[j], B[31 - j]) is a bitonic sequence holding
+// the 32 smallest of both, which a bitonic merge sorts.
+__device__ __forceinline__ void warp_merge_best(float& bd, int& bi, float v, int id, int K, int lane) {
+  float a = lane < K ? bd : FLT_MAX;
+  int ai = lane < K ? bi : INT_MAX;
+  const float rb = __shfl_sync(kFull, v, 31 - lane);
+  const int rbi = __shfl_sync(kFull, id, 31 - lane);
+  if (lex_less(rb, rbi, a, ai)) {
+    a = rb;
+    ai = rbi;
+  }
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const float ov = __shfl_xor_sync(kFull, a, j);
+    const int oi = __shfl_xor_sync(kFull, ai, j);
+    if (((lane & j) == 0) == lex_less(ov, oi, a, ai)) {
+      a = ov;
+      ai = oi;
+    }
+  }
+  bd = a;
+  bi = ai;
+}
+
 template <int D, int MC>
 __global__ __launch_bounds__(256) void k_rerank(
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
@@ -669,13 +715,18 @@ __global__ __launch_bounds__(256) void k_rerank(
     // the listed chunk with the smallest minimum (ties: lower split)
     float best = hv;
     int bs = lane;
+    if (nsplit == 1) {
+      best = __shfl_sync(kFull, hv, 0);
+      bs = 0;
+    } else {
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      const float ov = __shfl_xor_sync(kFull, best, off);
-      const int os = __shfl_xor_sync(kFull, bs, off);
-      if (ov < best || (ov == best && os < bs)) {
-        best = ov;
-        bs = os;
+      for (int off = 16; off; off >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, best, off);
+        const int os = __shfl_xor_sync(kFull, bs, off);
+        if (ov < best || (ov == best && os < bs)) {
+          best = ov;
+          bs = os;
+        }
       }
     }
     if (best == FLT_MAX) break;
@@ -721,7 +772,16 @@ __global__ __launch_bounds__(256) void k_rerank(
     }
     unsigned mm = __ballot_sync(kFull, mem);
     members += __popc(mm);
-    // insert the members in ascending (distance, ID) order
+    if (__popc(mm) > 4) {
+      // many (the first chunks): sort the chunk's members across the lanes
+      // and merge them with the K best
+      float v = mem ? dd : FLT_MAX;
+      int id = mem ? (int)e : INT_MAX;
+      warp_sort32(v, id, lane);
+      warp_merge_best(bd, bi, v, id, K, lane);
+      mm = 0;
+    }
+    // few: insert them one by one in ascending (distance, ID) order
     while (mm) {
       const bool mine = (mm >> lane) & 1u;
       float v = mine ? dd : FLT_MAX;
