@@ -63,7 +63,9 @@ typedef struct {
  * sigma blur_sigma, clamped borders) -> s x s box down-sampling.  LR patches
  * are lr_patch x lr_patch; HR patches are (scale*lr_patch)^2.  blur_sigma is
  * a double so that the taps are computed from the exact parameter value.
- * Supported: scale 1..4, lr_patch 2..7, blur_sigma > 0. */
+ * Supported: scale 1..4, blur_sigma > 0; dictionaries and queries need
+ * lr_patch 3 or 5 (UNSUPPORTED otherwise); the image-only calls
+ * (zoom_backproject, zoom_degrade, their adjoints) ignore lr_patch. */
 typedef struct {
   int32_t scale;
   int32_t lr_patch;
@@ -74,7 +76,11 @@ typedef struct {
  * h = floor((alpha.v + beta) / w).  min_table_hits = t (an ID is a candidate
  * if it shares the query's bin in >= t tables; 1 = plain union).
  * max_candidates: 0 = no cap; > 0 = the early stop of Sec. 4.2 (tables in
- * order, IDs ascending within a bin, stop at exactly max_candidates).
+ * order, IDs ascending within a bin, stop at exactly max_candidates distinct
+ * IDs; t is then not used).  With a cap the K nearest are searched among
+ * those IDs in FP32 (both precisions; a query whose bins hold fewer than K
+ * IDs is padded with the nearest entries outside them), the inference calls
+ * need K <= max_candidates and take nq * max_candidates * 4 bytes of scratch.
  * Supported: 1 <= L <= 32, 1 <= k <= 32, w > 0, 1 <= t <= L,
  * 0 <= max_candidates <= 4096. */
 typedef struct {
@@ -161,8 +167,9 @@ void zoom_dict_destroy(zoom_dict d);
 /* Copies stored arrays to the host (synchronises `stream`): lr_pix [N][P*P],
  * mu [N], hr_res [N][(s*P)^2]; any pointer may be NULL. */
 zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_res, void* stream);
-/* Dictionary sizes: N, LR patch side P, scale s. */
-zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale);
+/* Dictionary sizes: N, LR patch side P, scale s, and the blur sigma of its
+ * degradation; any pointer may be NULL. */
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma);
 
 /* ---- LSH index (Sec. 3.2; Sec. 4.1, Eq. 10) -----------------------------
  * Hashes every dictionary feature into L tables.  alpha: host float32
@@ -177,6 +184,31 @@ void zoom_index_destroy(zoom_index ix);
  * n_bins != NULL, the number of bins per table to host int32 [L]
  * (synchronises `stream`). */
 zoom_status zoom_index_export(zoom_index ix, uint64_t* keys, int32_t* n_bins, void* stream);
+/* The index's LSH parameters (any pointer may be NULL). */
+zoom_status zoom_index_info(zoom_index ix, zoom_lsh_params* lsh);
+
+/* ---- files: checkpoint / resume ------------------------------------------
+ * The paper keeps the N training pairs on disk once extracted (Sec. 2.1).
+ * zoom_dict_save writes every array the dictionary stores (LR pixels, the
+ * features, mu, squared feature norms and the HR residuals, float32) after a
+ * little-endian header ("ZOOMDICT", version 1, N, P, s, blur_sigma and the
+ * row strides); zoom_dict_load reads such a file into a new dictionary on
+ * ctx, bit-identical to the saved one.  zoom_index_save writes the LSH
+ * parameters and the projections ("ZOOMINDX", version 1, N, P*P, L, k,
+ * min_table_hits, max_candidates, w; then alpha [L*k][P*P], beta [L*k]);
+ * zoom_index_load rebuilds the index on dictionary d from them (the same
+ * keys and bins as the saved index).  All four synchronise `stream`; the
+ * caller owns `path` (a NUL-terminated file name).  Errors: IO (cannot
+ * open, write failure, truncated file), INVALID_ARG (not such a file,
+ * another version, sizes out of range, an index file of another
+ * dictionary), OOM, CUDA. */
+zoom_status zoom_dict_save(zoom_dict d, const char* path, void* stream);
+zoom_status zoom_dict_load(zoom_ctx ctx, const char* path, void* stream, zoom_dict* out);
+zoom_status zoom_index_save(zoom_index ix, const char* path, void* stream);
+zoom_status zoom_index_load(zoom_dict d, const char* path, void* stream, zoom_index* out);
+/* Copies the index's random draws to the host (synchronises `stream`):
+ * alpha float32 [L*k][P*P], beta float32 [L*k] (Eq. 10); either may be NULL. */
+zoom_status zoom_export_params(zoom_index ix, float* alpha, float* beta, void* stream);
 
 /* ---- inference ------------------------------------------------------------
  * zoom_upscale: the whole per-patch inference and back-projection of an LR

@@ -31,6 +31,7 @@ SOURCES = [
     "zoom_noalloc.cu",
     "kernels_backward.cu",
     "zoom_api_backward.cu",
+    "zoom_io.cu",
 ]
 HEADERS = ["zoom_internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -59,7 +59,13 @@ SIGNATURES = {
                                         _i64, _P(_i32), _vp, _P(_vp)]),
     "zoom_dict_destroy": (None, [_vp]),
     "zoom_dict_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
-    "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32)]),
+    "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(C.c_double)]),
+    "zoom_dict_save": (C.c_int, [_vp, C.c_char_p, _vp]),
+    "zoom_dict_load": (C.c_int, [_vp, C.c_char_p, _vp, _P(_vp)]),
+    "zoom_index_save": (C.c_int, [_vp, C.c_char_p, _vp]),
+    "zoom_index_load": (C.c_int, [_vp, C.c_char_p, _vp, _P(_vp)]),
+    "zoom_index_info": (C.c_int, [_vp, _P(LshParams)]),
+    "zoom_export_params": (C.c_int, [_vp, _vp, _vp, _vp]),
     "zoom_build_index": (C.c_int, [_vp, _P(LshParams), _vp, _vp, _vp, _P(_vp)]),
     "zoom_index_destroy": (None, [_vp]),
     "zoom_index_export": (C.c_int, [_vp, _vp, _vp, _vp]),

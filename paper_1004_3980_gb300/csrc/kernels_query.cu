@@ -191,6 +191,76 @@ __global__ __launch_bounds__(KNN_THREADS) void k_knn_exact(
 }
 
 // ---------------------------------------------------------------------------
+// Candidate set under the cap (the early stop of Sec. 4.2): the tables are
+// visited in order l = 0..L-1, each bin in ascending ID, and the first `cap`
+// distinct IDs form C(q); the K nearest of them in FP32 difference form,
+// ties by ID.  One thread per query; the collected IDs live in global
+// scratch [nq][cap].  A query with fewer than K candidates (its bins hold
+// fewer than K distinct IDs, cap >= K) is flagged: the SIMT scan then pads
+// it with the nearest entries outside its bins.
+// ---------------------------------------------------------------------------
+template <int D, int KMAX>
+__global__ __launch_bounds__(128) void k_knn_capped(
+    const float* __restrict__ qfeat, int dpad, int64_t nq, const uint64_t* __restrict__ qkeys,
+    const float* __restrict__ dfeat, int64_t N, int L, const uint64_t* __restrict__ ukeys,
+    const int32_t* __restrict__ offs, const int32_t* __restrict__ ids, const int32_t* __restrict__ nuniq,
+    int cap, int K, int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ cand,
+    int32_t* __restrict__ fb_list, unsigned long long* __restrict__ counters) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  int32_t* cs = cand + q * cap;
+  int nc = 0;
+  for (int l = 0; l < L && nc < cap; ++l) {
+    const uint64_t key = qkeys[q * L + l];
+    const uint64_t* uk = ukeys + (int64_t)l * N;
+    int lo = 0, hi = nuniq[l];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (uk[mid] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= nuniq[l] || uk[lo] != key) continue;
+    const int32_t* off = offs + (int64_t)l * (N + 1);
+    const int32_t* bin = ids + (int64_t)l * N;
+    const int nprev = nc;   // IDs of earlier tables; a bin holds distinct IDs
+    for (int p = off[lo]; p < off[lo + 1] && nc < cap; ++p) {
+      const int id = bin[p];
+      bool seen = false;
+      for (int j = 0; j < nprev && !seen; ++j) seen = cs[j] == id;
+      if (!seen) cs[nc++] = id;
+    }
+  }
+  if (nc < K) {
+    const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
+    fb_list[slot] = (int32_t)q;
+    return;
+  }
+  float qv[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) qv[i] = qfeat[q * dpad + i];
+  Cand bl[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) bl[j] = Cand{FLT_MAX, INT_MAX, 2};
+  for (int j = 0; j < nc; ++j) {
+    const int id = cs[j];
+    float dd = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float df = qv[i] - dfeat[(int64_t)id * dpad + i];
+      dd = fmaf(df, df, dd);
+    }
+    const Cand cd{dd, id, 0};
+    if (cand_less(cd, list_worst<KMAX>(bl, K))) list_insert<KMAX>(bl, K, cd);
+  }
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j)
+    if (j < K) {
+      nbr[q * K + j] = bl[j].id;
+      dist[q * K + j] = bl[j].d;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // LLE weights (Eq. 12-13): G = Z Z^T over the K neighbours, C = G + eps I,
 // eps = reg_rel * trace(G), Cholesky, C z = 1, w = z / sum(z).  One thread
 // per query.  FP64 when the condition bound (trace + eps) / eps exceeds the
@@ -342,14 +412,34 @@ cudaError_t knn_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qk
                            const int32_t* qidx, const unsigned long long* qcount, cudaStream_t st) {
   zoom_dict d = ix->dict;
   int blocks = (int)((nq + KNN_THREADS - 1) / KNN_THREADS);
+  // under the cap the candidate rule ignores t (only capped queries whose
+  // bins hold fewer than K IDs come here: their candidates are the union)
+  const int tmin = ix->cap > 0 ? 1 : ix->t;
   if (K <= 8)
     k_knn_exact<D, 8><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
-                                                     ix->dkeys, ix->L, ix->t, K, nbr, dist,
+                                                     ix->dkeys, ix->L, tmin, K, nbr, dist,
                                                      counters, qidx, qcount);
   else
     k_knn_exact<D, 16><<<blocks, KNN_THREADS, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n,
-                                                      ix->dkeys, ix->L, ix->t, K, nbr, dist,
+                                                      ix->dkeys, ix->L, tmin, K, nbr, dist,
                                                       counters, qidx, qcount);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t capped_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
+                              int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
+                              unsigned long long* counters, cudaStream_t st) {
+  zoom_dict d = ix->dict;
+  const int blocks = (int)((nq + 127) / 128);
+  if (K <= 8)
+    k_knn_capped<D, 8><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n, ix->L, ix->ukeys,
+                                               ix->offs, ix->ids, ix->nuniq, ix->cap, K, nbr, dist, cand,
+                                               fb, counters);
+  else
+    k_knn_capped<D, 16><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n, ix->L, ix->ukeys,
+                                                ix->offs, ix->ids, ix->nuniq, ix->cap, K, nbr, dist, cand,
+                                                fb, counters);
   return cudaGetLastError();
 }
 
@@ -399,6 +489,16 @@ cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* 
     return knn_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, qidx, qcount, st);
   if (ix->dict->d == 25)
     return knn_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, counters, qidx, qcount, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_knn_capped(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
+                              int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
+                              unsigned long long* counters, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  if (ix->dict->d == 9) return capped_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
+  if (ix->dict->d == 25)
+    return capped_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
   return cudaErrorInvalidValue;
 }
 

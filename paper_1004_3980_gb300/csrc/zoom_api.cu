@@ -55,6 +55,43 @@ struct Carver {
   }
 };
 
+}  // namespace
+
+zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, cudaStream_t st) {
+  zoom_dict d = new zoom_dict_s();
+  d->ctx = ctx;
+  d->n = n;
+  d->P = P;
+  d->s = s;
+  d->d = P * P;
+  d->dpad = (d->d + 3) / 4 * 4;
+  d->PH = s * P;
+  d->ph2 = d->PH * d->PH;
+  d->ph2pad = (d->ph2 + 3) / 4 * 4;
+  d->blur_sigma = blur_sigma;
+  Carver c0(nullptr);
+  c0.take<float>(n * d->d);
+  c0.take<float>(n * d->dpad);
+  c0.take<float>(n);
+  c0.take<float>(n);
+  c0.take<float>(n * d->ph2pad);
+  d->bytes = c0.off + 256;
+  void* mem = zoom_alloc(ctx, d->bytes, st);
+  if (!mem) {
+    delete d;
+    return nullptr;
+  }
+  Carver c(mem);
+  d->lr_pix = c.take<float>(n * d->d);   // first: the allocation's base
+  d->feat = c.take<float>(n * d->dpad);
+  d->mu = c.take<float>(n);
+  d->norm2 = c.take<float>(n);
+  d->hr_res = c.take<float>(n * d->ph2pad);
+  return d;
+}
+
+namespace {
+
 bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string& why) {
   if (!p) { why = "params is NULL"; return false; }
   if (p->K < 1 || p->K > 16) { why = "K must be in 1..16"; return false; }
@@ -195,37 +232,9 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   }
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(ctx->device));
-  zoom_dict d = new zoom_dict_s();
-  d->ctx = ctx;
-  d->n = n_pairs;
-  d->P = P;
-  d->s = s;
-  d->d = P * P;
-  d->dpad = (d->d + 3) / 4 * 4;
-  d->PH = s * P;
-  d->ph2 = d->PH * d->PH;
-  d->ph2pad = (d->ph2 + 3) / 4 * 4;
-  d->blur_sigma = degr->blur_sigma;
-  {
-    Carver c(nullptr);
-    c.take<float>(n_pairs * d->d);
-    c.take<float>(n_pairs * d->dpad);
-    c.take<float>(n_pairs);
-    c.take<float>(n_pairs);
-    c.take<float>(n_pairs * d->ph2pad);
-    d->bytes = c.off + 256;
-  }
-  void* mem = zoom_alloc(ctx, d->bytes, st);
-  if (!mem) {
-    delete d;
-    return fail(ZOOM_ERR_OOM, "dictionary arrays");
-  }
-  Carver c(mem);
-  d->lr_pix = c.take<float>(n_pairs * d->d);
-  d->feat = c.take<float>(n_pairs * d->dpad);
-  d->mu = c.take<float>(n_pairs);
-  d->norm2 = c.take<float>(n_pairs);
-  d->hr_res = c.take<float>(n_pairs * d->ph2pad);
+  zoom_dict d = zoom_dict_alloc(ctx, n_pairs, P, s, degr->blur_sigma, st);
+  if (!d) return fail(ZOOM_ERR_OOM, "dictionary arrays");
+  void* mem = d->lr_pix;
 
   // scratch: LR images, pointer/width tables, positions
   size_t lr_total = 0;
@@ -302,11 +311,24 @@ void zoom_dict_destroy(zoom_dict d) {
   delete d;
 }
 
-zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale) {
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma) {
   if (!d) return fail(ZOOM_ERR_INVALID_ARG, "NULL dictionary");
   if (n) *n = d->n;
   if (patch) *patch = d->P;
   if (scale) *scale = d->s;
+  if (blur_sigma) *blur_sigma = d->blur_sigma;
+  return ZOOM_OK;
+}
+
+zoom_status zoom_index_info(zoom_index ix, zoom_lsh_params* lsh) {
+  if (!ix) return fail(ZOOM_ERR_INVALID_ARG, "NULL index");
+  if (lsh) {
+    lsh->L = ix->L;
+    lsh->k = ix->k;
+    lsh->w = ix->w;
+    lsh->min_table_hits = ix->t;
+    lsh->max_candidates = ix->cap;
+  }
   return ZOOM_OK;
 }
 
@@ -338,8 +360,6 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     return fail(ZOOM_ERR_INVALID_ARG, "min_table_hits must be in 1..L");
   if (lsh->max_candidates < 0 || lsh->max_candidates > 4096)
     return fail(ZOOM_ERR_INVALID_ARG, "max_candidates must be in 0..4096");
-  if (lsh->max_candidates > 0)
-    return fail(ZOOM_ERR_UNSUPPORTED, "the candidate cap is not supported by this build");
   const size_t smem = (size_t)lsh->L * lsh->k * (d->d + 1) * 4;
   if (smem > 200 * 1024) return fail(ZOOM_ERR_INVALID_ARG, "L*k*(d+1) too large");
   zoom_ctx ctx = d->ctx;
@@ -452,6 +472,7 @@ struct QueryBufs {
 // with MC-entry lists over nsplit dictionary splits, and its scratch size.
 struct SearchPlan {
   bool tc = false;
+  bool capped = false;   // the index caps the candidate set (Sec. 4.2 early stop)
   int prec = 0, MC = 16, nsplit = 1, KCH = 80;
   int64_t q_rows = 0;
   size_t bytes = 0;
@@ -461,6 +482,14 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
                        int mc_override) {
   zoom_dict d = ix->dict;
   SearchPlan p;
+  if (ix->cap > 0) {
+    p.capped = true;
+    Carver c(nullptr);
+    c.take<int32_t>((size_t)nq * ix->cap);
+    c.take<int32_t>(nq);
+    p.bytes = c.off + 256;
+    return p;
+  }
   p.tc = prm->precision == 1 || prm->search == 2 || (prm->search == 0 && d->n >= 4096);
   if (!p.tc) return p;
   p.prec = prm->precision;
@@ -471,10 +500,10 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   // same pace, so L2 serves nearly all of them whatever the dictionary size.
   // The persistent CTAs take (query pair, split) items in turn, so the last
   // round decides the run time: the split count minimises the tiles of the
-  // busiest CTA, each item charged a restart of its best lists (about
-  // MC*ln(N/MC) insertions per query, spread over the whole split as warp-
-  // divergent appends), measured at about kRestartTiles dictionary tiles.
-  constexpr int64_t kRestartTiles = 2048;
+  // busiest CTA, each item charged a restart of its best chunk lists (about
+  // MC*(1 + ln(N/32/MC)) merged chunks per query, most in the first tiles),
+  // measured at about kRestartTiles dictionary tiles.
+  constexpr int64_t kRestartTiles = 768;
   int64_t nsplit = nsplit_override;
   if (nsplit <= 0) {
     int64_t best_cost = INT64_MAX;
@@ -511,6 +540,16 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   zoom_dict d = ix->dict;
   zoom_ctx ctx = d->ctx;
   const int K = prm->K;
+  if (pl.capped) {
+    Carver s1(ws);
+    int32_t* cand = s1.take<int32_t>((size_t)nq * ix->cap);
+    int32_t* fb = s1.take<int32_t>(nq);
+    cudaError_t e = launch_knn_capped(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, cand, fb, ctx->d_counters, st);
+    if (e == cudaSuccess)
+      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
+                           ctx->d_counters + CNT_FALLBACK, st);
+    return e;
+  }
   if (!pl.tc)
     return launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, nullptr,
                             nullptr, st);
@@ -539,7 +578,7 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
 cudaError_t run_search(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
                        cudaStream_t st, bool& oom) {
   const SearchPlan pl = plan_search(ix, prm, nq, 0, 0);
-  if (!pl.tc) return run_search_ws(ix, prm, b, nq, pl, nullptr, st);
+  if (!pl.tc && !pl.capped) return run_search_ws(ix, prm, b, nq, pl, nullptr, st);
   Scratch scr(ix->dict->ctx, st);
   if (!scr.get(pl.bytes)) {
     oom = true;
@@ -598,6 +637,7 @@ zoom_status zoom_query(zoom_index ix, const float* lr, int32_t h, int32_t w,
   zoom_dict d = ix->dict;
   std::string why;
   if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+  if (ix->cap > 0 && prm->K > ix->cap) return fail(ZOOM_ERR_INVALID_ARG, "K exceeds max_candidates");
   if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
@@ -687,6 +727,7 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   zoom_dict d = ix->dict;
   std::string why;
   if (!check_upscale_params(prm, d, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+  if (ix->cap > 0 && prm->K > ix->cap) return fail(ZOOM_ERR_INVALID_ARG, "K exceeds max_candidates");
   if (scale != d->s) return fail(ZOOM_ERR_INVALID_ARG, "scale differs from the dictionary's");
   if (h < d->P || w < d->P) return fail(ZOOM_ERR_INVALID_ARG, "image smaller than one patch");
   cudaStream_t st = (cudaStream_t)stream;
@@ -878,6 +919,7 @@ int64_t qbucket(int64_t nq) {
 // sample of its queries and remembers the fastest.
 zoom_status autotune_group(Group& g, const zoom_upscale_params* prm, cudaStream_t st) {
   zoom_ctx ctx = g.ix->dict->ctx;
+  if (g.ix->cap > 0) return ZOOM_OK;   // the capped walk has nothing to tune
   TuneMap& tm = *(TuneMap*)ctx->tuned;
   const TuneKey key{g.ix, qbucket(g.nq), prm->precision, prm->K};
   if (tm.count(key)) return ZOOM_OK;
@@ -938,6 +980,8 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
     if (ixs[j]->dict->ctx != ctx) return fail(ZOOM_ERR_INVALID_ARG, "indexes of different contexts");
     std::string why;
     if (!check_upscale_params(prm, ixs[j]->dict, why)) return fail(ZOOM_ERR_INVALID_ARG, why);
+    if (ixs[j]->cap > 0 && prm->K > ixs[j]->cap)
+      return fail(ZOOM_ERR_INVALID_ARG, "K exceeds max_candidates");
   }
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(ctx->device));

@@ -84,6 +84,9 @@ struct zoom_index_s {
 // ---------------------------------------------------------------------------
 
 void zoom_set_error(const std::string& msg);
+// A dictionary handle of n pairs with its (uninitialised) device arrays in
+// one allocation based at lr_pix; nullptr when the allocation fails.
+zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, cudaStream_t st);
 void* zoom_alloc(zoom_ctx ctx, size_t bytes, cudaStream_t st);
 void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st);
 
@@ -113,6 +116,11 @@ cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* 
                              int K, int32_t* nbr, float* dist, unsigned long long* counters,
                              const int32_t* qidx, const unsigned long long* qcount,
                              cudaStream_t st);
+// capped candidate walk (index cap > 0): cand = scratch [nq][cap]; queries
+// with fewer than K candidates are appended to fb (count in counters)
+cudaError_t launch_knn_capped(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
+                              int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
+                              unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
                        const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
                        unsigned long long* counters, cudaStream_t st);

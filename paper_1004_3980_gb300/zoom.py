@@ -7,6 +7,7 @@ from __future__ import annotations
 import atexit
 import ctypes as C
 import dataclasses
+import os
 import sys
 import weakref
 
@@ -142,9 +143,28 @@ class Dictionary:
         h = C.c_void_p()
         capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), len(pos),
                   pos.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream), C.byref(h))
+        self._adopt(h)
+
+    def _adopt(self, h):
         self.handle = h
         _LIVE["dict"].add(self)
-        self.n, self.patch, self.scale, self.blur_sigma = len(pos), patch, scale, blur_sigma
+        n, P, s, sig = C.c_int64(), C.c_int32(), C.c_int32(), C.c_double()
+        capi.call("zoom_dict_info", h, C.byref(n), C.byref(P), C.byref(s), C.byref(sig))
+        self.n, self.patch, self.scale, self.blur_sigma = n.value, P.value, s.value, sig.value
+
+    def save(self, path: str, stream=None) -> None:
+        """Writes every stored array to a file (zoom_dict_save)."""
+        capi.call("zoom_dict_save", self.handle, os.fsencode(path), _stream(stream))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str, stream=None) -> "Dictionary":
+        """A dictionary read from a file written by save (zoom_dict_load)."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        h = C.c_void_p()
+        capi.call("zoom_dict_load", ctx.handle, os.fsencode(path), _stream(stream), C.byref(h))
+        self._adopt(h)
+        return self
 
     def export(self, stream=None):
         d, ph = self.patch ** 2, (self.scale * self.patch) ** 2
@@ -183,9 +203,37 @@ class Index:
         h = C.c_void_p()
         capi.call("zoom_build_index", dictionary.handle, C.byref(prm), a.ctypes.data, b.ctypes.data,
                   _stream(stream), C.byref(h))
+        self._adopt(h)
+
+    def _adopt(self, h):
         self.handle = h
         _LIVE["index"].add(self)
-        self.L, self.k, self.w = L, k, w
+        prm = capi.LshParams()
+        capi.call("zoom_index_info", h, C.byref(prm))
+        self.L, self.k, self.w = prm.L, prm.k, prm.w
+        self.min_table_hits, self.max_candidates = prm.min_table_hits, prm.max_candidates
+
+    def save(self, path: str, stream=None) -> None:
+        """Writes the LSH parameters and projections to a file (zoom_index_save)."""
+        capi.call("zoom_index_save", self.handle, os.fsencode(path), _stream(stream))
+
+    @classmethod
+    def load(cls, dictionary: Dictionary, path: str, stream=None) -> "Index":
+        """The index of a file written by save, rebuilt on `dictionary` (zoom_index_load)."""
+        self = cls.__new__(cls)
+        self.dictionary = dictionary
+        h = C.c_void_p()
+        capi.call("zoom_index_load", dictionary.handle, os.fsencode(path), _stream(stream), C.byref(h))
+        self._adopt(h)
+        return self
+
+    def params(self, stream=None):
+        """The random draws (alpha [L*k][P*P], beta [L*k]) as numpy float32 (zoom_export_params)."""
+        d = self.dictionary.patch ** 2
+        alpha = np.empty((self.L * self.k, d), np.float32)
+        beta = np.empty(self.L * self.k, np.float32)
+        capi.call("zoom_export_params", self.handle, alpha.ctypes.data, beta.ctypes.data, _stream(stream))
+        return alpha, beta
 
     def export_keys(self, stream=None):
         keys = np.empty((self.dictionary.n, self.L), np.uint64)
