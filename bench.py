@@ -364,6 +364,18 @@ def run_single(a, wl, config, rank, world, local):
         ms2 = timed_steps(lambda: Z.upscale(ix, lr, p2, out=out), 1, st, torch)
         res["fp32_simt_scan"] = {"value": world * hr_px / 1e6 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
                                  "identical_to_exact_form": bool(torch.equal(out, hr_exact))}
+        # the paper's early stop: candidate set capped at 3L IDs (tables in
+        # order, IDs ascending within a bin), K nearest among them
+        cap = 3 * wl.L
+        ixc = Z.Index(d, wl.L, wl.k, wl.w, alpha, beta, max_candidates=cap)
+        for _ in range(2):
+            Z.upscale(ixc, lr, prm, out=out)
+        ms3 = timed_steps(lambda: Z.upscale(ixc, lr, prm, out=out), a.steps, st, torch)
+        mse3 = float(((out - hr_exact) ** 2).mean())
+        res["capped_3L"] = {"value": world * hr_px / 1e6 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
+                            "max_candidates": cap, "distances_per_query": cap,
+                            "psnr_vs_uncapped_db": 10 * np.log10(1.0 / max(mse3, 1e-30))}
+        ixc.close()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_oracle_sample(wl, train, pos, alpha, beta, lr_np, a.cpu_sample_queries)
     return res

@@ -71,23 +71,37 @@ struct Gauss1D {
   float c[16];
 };
 
+// The window radius is a template parameter: the clamped columns and their
+// LR columns are computed once per pixel (2R+1 divisions instead of
+// (2R+1)^2), in the same summation order as a direct double loop.
+template <int R>
 __global__ void k_bp_update(const float* __restrict__ x, float* __restrict__ xo, int H, int W,
                             const float* __restrict__ e, int w, int s, Gauss1D g,
                             float inv_two_sr2) {
   const int X = blockIdx.x * blockDim.x + threadIdx.x;
   const int Y = blockIdx.y * blockDim.y + threadIdx.y;
   if (X >= W || Y >= H) return;
-  const int R = g.R;
+  constexpr int T = 2 * R + 1;
+  int cx[T], ce[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int xx = zoom_clampi(X + t - R, 0, W - 1);
+    cx[t] = xx;
+    ce[t] = xx / s;
+  }
   float gs = 0.f, box = 0.f;
-  for (int dy = -R; dy <= R; ++dy) {
-    const int yy = zoom_clampi(Y + dy, 0, H - 1);
+#pragma unroll
+  for (int u = 0; u < T; ++u) {
+    const int yy = zoom_clampi(Y + u - R, 0, H - 1);
+    const float* xr = x + (int64_t)yy * W;
+    const float* er = e + (int64_t)(yy / s) * w;
     float grow = 0.f, brow = 0.f;
-    for (int dx = -R; dx <= R; ++dx) {
-      const int xx = zoom_clampi(X + dx, 0, W - 1);
-      grow = fmaf(g.c[dx + R], e[(int64_t)(yy / s) * w + xx / s], grow);
-      brow += x[(int64_t)yy * W + xx];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      grow = fmaf(g.c[t], er[ce[t]], grow);
+      brow += xr[cx[t]];
     }
-    gs = fmaf(g.c[dy + R], grow, gs);
+    gs = fmaf(g.c[u], grow, gs);
     box += brow;
   }
   const float m = box / (float)((2 * R + 1) * (2 * R + 1));
@@ -136,6 +150,13 @@ cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, f
   k_bp_error<<<g1, blk, 0, st>>>(x, H, W, lr, h, w, s, wt, err);
   dim3 g2((W + 31) / 32, (H + 7) / 8);
   const float inv = (float)(1.0 / (2.0 * (double)sigma_r * (double)sigma_r));
-  k_bp_update<<<g2, blk, 0, st>>>(x, x_out, H, W, err, w, s, g, inv);
+  switch (radius) {
+#define ZOOM_BPU(RR) \
+  case RR: k_bp_update<RR><<<g2, blk, 0, st>>>(x, x_out, H, W, err, w, s, g, inv); break;
+    ZOOM_BPU(1) ZOOM_BPU(2) ZOOM_BPU(3) ZOOM_BPU(4) ZOOM_BPU(5) ZOOM_BPU(6) ZOOM_BPU(7)
+#undef ZOOM_BPU
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
