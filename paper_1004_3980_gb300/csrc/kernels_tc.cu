@@ -32,11 +32,16 @@
 
 namespace {
 
-// warp 0 producer, warps 1 and 10 MMA issue (query tile 0 and 1), warps 2..9
-// epilogue.  One thread issuing every MMA, wait and commit of a dictionary
-// tile was measured to bound the kernel (about 60 cycles per issued MMA), so
-// the two query tiles have an issuing thread each.
-constexpr int TC_THREADS = 352;
+// Warp 0 producer, warps 2..9 epilogue, and MMA-issuing warps: one thread
+// issues a 128x128x16 MMA in about 75 cycles (the tensor core executes it in
+// 64), plus about 250 cycles of waits, fence and commit per tile, so one
+// issuing thread per (accumulator buffer, query tile) -- warps 1, 10, 11, 12
+// -- keeps the tensor pipe fed.  Thirteen warps sit 4/3/3/3 on the SM
+// sub-partitions (16K registers each), which caps a thread at 128 registers:
+// the 32-entry lists do not fit, so they keep two issuing warps (1 and 10,
+// one per query tile; 11 warps, 168 registers).
+__host__ __device__ constexpr int tc_mma_warps(int MC) { return MC <= 16 ? 4 : 2; }
+__host__ __device__ constexpr int tc_threads(int MC) { return (9 + tc_mma_warps(MC)) * 32; }
 // Dictionary-tile ring depth: enough bulk copies in flight to cover their
 // latency, within the shared memory left by the query tiles and the buffers.
 __host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 7 : 16; }
@@ -290,9 +295,8 @@ __device__ __forceinline__ void chunk_test(float m, int chunk, float thr, float*
 }
 
 template <int KC, int MC, uint32_t AB_TYPE>
-// Eleven warps sit 3/3/3/2 on the four SM sub-partitions (16K registers
-// each), which caps a thread at 168 registers.
-__global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
+__global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a) {
+  constexpr int kMma = tc_mma_warps(MC);
   constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
   constexpr int kKSteps = KC / 2;                     // MMA K = 16 = two 8-element chunks
   constexpr uint32_t kIdesc = instr_desc(AB_TYPE);
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
-    mbar_init(a_empty, 2);    // one commit per MMA thread
+    mbar_init(a_empty, kMma);   // one commit per MMA thread
     for (int s = 0; s < kStages; ++s) {
       mbar_init(b_full + s, 1);
       mbar_init(b_empty + s, 2);
@@ -370,10 +374,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         }
       }
     }
-  } else if (warp == 1 || warp == 10) {
-    // ---------------- MMA issue: one thread per query tile ----------------
+  } else if (warp == 1 || warp >= 10) {
+    // ------- MMA issue: one thread per query tile (and buffer, kMma = 4) -------
     if (lane == 0) {
-      const int qt = warp == 1 ? 0 : 1;
+      const int m = warp == 1 ? 0 : warp - 9;   // warps 1, 10, 11, 12
+      const int qt = m & 1;
+      const int mine_buf = kMma == 4 ? (m >> 1) : -1;   // -1: both buffers
       int stage = 0, buf = 0, items = 0;
       uint32_t phase = 0, a_phase = 0;
       uint32_t accp[2] = {0u, 0u};
@@ -394,18 +400,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_knn_tc(TcArgs a) {
         tc_fence_after();
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
-          if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status) ||
-              !mbar_wait_fast(acc_empty + buf * 2 + qt, accp[buf] ^ 1u, abort_flag, a.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t bd_s = bd0 + (uint64_t)stage * kTileAdv;
-          const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
+          if (mine_buf < 0 || buf == mine_buf) {
+            if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status) ||
+                !mbar_wait_fast(acc_empty + buf * 2 + qt, accp[buf] ^ 1u, abort_flag, a.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t bd_s = bd0 + (uint64_t)stage * kTileAdv;
+            const uint32_t d_addr = tmem + (uint32_t)(buf * 256 + qt * 128);
 #pragma unroll
-          for (int ks = 0; ks < kKSteps; ++ks)
-            mma_f16(d_addr, ad0 + ks * kKStepAdv, bd_s + ks * kKStepAdv, kIdesc, ks > 0 ? 1u : 0u);
-          mma_commit(acc_full + buf * 2 + qt);   // also frees the ring stage (epilogue)
+            for (int ks = 0; ks < kKSteps; ++ks)
+              mma_f16(d_addr, ad0 + ks * kKStepAdv, bd_s + ks * kKStepAdv, kIdesc, ks > 0 ? 1u : 0u);
+            mma_commit(acc_full + buf * 2 + qt);   // also frees the ring stage (epilogue)
+          }
           accp[buf] ^= 1u;
           buf ^= 1;
           if (++stage == kStages) {
@@ -882,7 +890,7 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
   auto kern = k_knn_tc<KC, MC, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, TC_THREADS, smem, st>>>(args);
+  kern<<<grid, tc_threads(MC), smem, st>>>(args);
   return cudaGetLastError();
 }
 
