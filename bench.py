@@ -189,15 +189,38 @@ def launches_per_step(wl: S.Workload, tc: bool) -> int:
     return 3 + (4 if tc else 1) + 2 + 2 * wl.bp_iters
 
 
-def timed_steps(fn, steps, st, torch):
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """The slowest rank's time (replicas: the job ends when the last one does);
+    `device` is the tensor device of the process group's backend."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Units all ranks processed per second (weak scaling: every replica does
+    the same per-rank work in the step)."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
+def timed_steps(fn, steps, st, torch, world: int = 1):
+    """Mean ms per step of `fn` with CUDA events on `st`; with several ranks
+    the region is bracketed by barriers and the slowest rank's time is kept."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record(st)
     for _ in range(steps):
         fn()
     e1.record(st)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps
+    if world > 1:
+        torch.distributed.barrier()
+    return max_over_ranks(e0.elapsed_time(e1) / steps, world, "cuda")
 
 
 def reference_arm(a, wl, config, hr_px, rank):
@@ -279,14 +302,10 @@ def run_single(a, wl, config, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ctx.set_stage_timing(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
     ms_step = ms_total / a.steps
-    value = world * hr_px / 1e6 / (ms_step / 1e3)
+    value = whole_job_rate(hr_px / 1e6, world, ms_step)
     stage = {k2: v / a.steps for k2, v in stage_ms.items()}
     hr_exact = out.clone()
 
@@ -352,7 +371,7 @@ def run_single(a, wl, config, rank, world, local):
         p1 = params(precision=1, rerank_mult=2)
         for _ in range(2):
             Z.upscale(ix, lr, p1, out=out)
-        ms1 = timed_steps(lambda: Z.upscale(ix, lr, p1, out=out), a.steps, st, torch)
+        ms1 = timed_steps(lambda: Z.upscale(ix, lr, p1, out=out), a.steps, st, torch, world)
         mse = float(((out - hr_exact) ** 2).mean())
         qe = Z.query(ix, lr, prm)["nbr"].cpu().numpy()
         qb = Z.query(ix, lr, p1)["nbr"].cpu().numpy()
@@ -361,7 +380,7 @@ def run_single(a, wl, config, rank, world, local):
                        "recall_vs_exact": rec, "psnr_vs_exact_db": 10 * np.log10(1.0 / max(mse, 1e-30))}
         # one step of the plain SIMT scan (exact, no tensor cores)
         p2 = params(search=1)
-        ms2 = timed_steps(lambda: Z.upscale(ix, lr, p2, out=out), 1, st, torch)
+        ms2 = timed_steps(lambda: Z.upscale(ix, lr, p2, out=out), 1, st, torch, world)
         res["fp32_simt_scan"] = {"value": world * hr_px / 1e6 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
                                  "identical_to_exact_form": bool(torch.equal(out, hr_exact))}
         # the paper's early stop: candidate set capped at 3L IDs (tables in
@@ -370,7 +389,7 @@ def run_single(a, wl, config, rank, world, local):
         ixc = Z.Index(d, wl.L, wl.k, wl.w, alpha, beta, max_candidates=cap)
         for _ in range(2):
             Z.upscale(ixc, lr, prm, out=out)
-        ms3 = timed_steps(lambda: Z.upscale(ixc, lr, prm, out=out), a.steps, st, torch)
+        ms3 = timed_steps(lambda: Z.upscale(ixc, lr, prm, out=out), a.steps, st, torch, world)
         mse3 = float(((out - hr_exact) ** 2).mean())
         res["capped_3L"] = {"value": world * hr_px / 1e6 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
                             "max_candidates": cap, "distances_per_query": cap,
@@ -410,10 +429,10 @@ def run_batch(a, config, rank, world, local):
         Z.upscale_batch(indexes, lrs, p1, outs=outs)
     clocks = ClockSampler(local)
     clocks.start()
-    ms = timed_steps(lambda: Z.upscale_batch(indexes, lrs, p1, outs=outs), a.steps, st, torch)
+    ms = timed_steps(lambda: Z.upscale_batch(indexes, lrs, p1, outs=outs), a.steps, st, torch, world)
     clk = clocks.stop()
     _, lat = Z.upscale_batch(indexes, lrs, p1, outs=outs, want_latency=True)
-    value = world * hr_px / 1e6 / (ms / 1e3)
+    value = whole_job_rate(hr_px / 1e6, world, ms)
     # the exact FP32 form looped image by image, for comparison
     p0 = Z.UpscaleParams(K=8, bp_iters=5)
     by = {ix.dictionary.scale: ix for ix in indexes}
@@ -424,7 +443,7 @@ def run_batch(a, config, rank, world, local):
             Z.upscale(by[s], x, p0, out=o)
 
     loop()
-    ms_loop = timed_steps(loop, 1, st, torch)
+    ms_loop = timed_steps(loop, 1, st, torch, world)
     mse = float(sum(((o - lo) ** 2).sum() for o, lo in zip(outs, loop_outs)) / hr_px)
     Z.batch_release(ctx)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
