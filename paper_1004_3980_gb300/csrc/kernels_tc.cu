@@ -241,6 +241,47 @@ struct TcArgs {
   float* out_d;          // [nsplit][nq][MC] chunk minimum d~, ascending (FLT_MAX: none)
   int32_t* out_id;       // [nsplit][nq][MC] chunk index (entries 32c..32c+31; -1: none)
   unsigned int* status;
+  // tail_split (> 0): the first full_rounds * gridDim.x query pairs are
+  // whole items (one per CTA and round, every CTA streaming the dictionary
+  // from tile 0 in step, so L2 serves the tiles); the remaining pairs are
+  // cut into tail_split equal dictionary parts, nsplit = tail_split lists,
+  // so the last round is shorter.  0: items are (split, pair) round robin.
+  int tail_split;
+  int full_rounds;
+};
+
+// The work items of one CTA, in order; every role walks the same sequence.
+struct WorkIter {
+  int k = 0;   // item number of this CTA
+  // qp: query pair, seg: list index, [t0, t1): dictionary tiles
+  __device__ bool next(const TcArgs& a, int& qp, int& seg, int& t0, int& t1) {
+    const int G = gridDim.x, c = blockIdx.x;
+    if (a.tail_split > 0) {
+      if (k < a.full_rounds) {
+        qp = c + k * G;
+        seg = 0;
+        t0 = 0;
+        t1 = a.nd_tiles;
+      } else {
+        const int tail = a.nq_pairs - a.full_rounds * G;
+        const int j = c + (k - a.full_rounds) * G;   // tail item: part j / tail of pair j % tail
+        if (j >= tail * a.tail_split) return false;
+        qp = a.full_rounds * G + j % tail;
+        seg = j / tail;
+        t0 = seg * a.tiles_per_split;
+        t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+      }
+    } else {
+      const int item = c + k * G;
+      if (item >= a.nsplit * a.nq_pairs) return false;
+      seg = item / a.nq_pairs;
+      qp = item % a.nq_pairs;
+      t0 = seg * a.tiles_per_split;
+      t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+    }
+    ++k;
+    return true;
+  }
 };
 
 // Inserts (v, id) into the ascending list, dropping its last entry; nothing
@@ -343,7 +384,6 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int n_items = a.nsplit * a.nq_pairs;
 
   if (warp == 0) {
     // ---------------- producer: bulk copies of operand tiles ----------------
@@ -351,10 +391,9 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
       int stage = 0;
       uint32_t phase = 0, a_phase = 0;
       bool first = true;
-      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-        const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
-        const int t0 = split * a.tiles_per_split;
-        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+      WorkIter it;
+      int qp, seg, t0, t1;
+      while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
         if (!first) {
           if (!mbar_wait(a_empty, a_phase, abort_flag, a.status)) break;
           a_phase ^= 1u;
@@ -391,10 +430,9 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
       const uint64_t bd0 = smem_desc(smem_u32(sB), TC_ROWS * 16, 128);
       constexpr uint64_t kKStepAdv = (2 * TC_ROWS * 16) >> 4;
       constexpr uint64_t kTileAdv = kTileBytes >> 4;
-      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-        const int split = item / a.nq_pairs;
-        const int t0 = split * a.tiles_per_split;
-        const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
+      WorkIter it;
+      int qp, seg, t0, t1;
+      while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
         if (!mbar_wait_fast(a_full, a_phase, abort_flag, a.status)) break;
         a_phase ^= 1u;
         tc_fence_after();
@@ -445,11 +483,10 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
     // (two arrivals free it), which keeps that commit off the MMA threads.
     int stage = 0;
     const bool releaser = (ew & 3) == 0 && lane == 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    WorkIter it;
+    int qp, split, t0, t1;
+    while (it.next(a, qp, split, t0, t1)) {
       if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
-      const int split = item / a.nq_pairs, qp = item % a.nq_pairs;
-      const int t0 = split * a.tiles_per_split;
-      const int t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
       const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
       const bool valid = q < a.nq;
       const float qn = valid ? a.qn[q] : 0.f;
@@ -507,6 +544,18 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
           const bool real = li[j] >= 0 && (int64_t)li[j] * 32 < a.nd;
           od[j] = real ? qn + ld[j] : FLT_MAX;
           oi[j] = real ? li[j] : -1;
+        }
+        if (a.tail_split > 0 && t0 == 0 && t1 == a.nd_tiles) {
+          // a whole pair: its other lists are empty
+          for (int s2 = 1; s2 < a.tail_split; ++s2) {
+            float* od1 = a.out_d + ((int64_t)s2 * a.nq + q) * MC;
+            int32_t* oi1 = a.out_id + ((int64_t)s2 * a.nq + q) * MC;
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+              od1[j] = FLT_MAX;
+              oi1[j] = -1;
+            }
+          }
         }
       }
     }
@@ -895,8 +944,8 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
 }
 
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
-                          int64_t nd, int precision, int MC, int nsplit, int grid, float* out_d,
-                          int32_t* out_id, unsigned int* status, cudaStream_t st) {
+                          int64_t nd, int precision, int MC, int nsplit, int tail_split, int grid,
+                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st) {
   TcArgs a;
   a.qop = qop;
   a.qn = qn;
@@ -910,9 +959,12 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
   a.out_d = out_d;
   a.out_id = out_id;
   a.status = status;
+  a.tail_split = tail_split;
+  if (tail_split > 0 && nsplit != tail_split) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(precision);
-  const int items = a.nsplit * a.nq_pairs;
+  const int items = tail_split > 0 ? a.nq_pairs : a.nsplit * a.nq_pairs;
   grid = grid < items ? grid : items;
+  a.full_rounds = tail_split > 0 ? a.nq_pairs / grid : 0;
   if (precision == 0) {
     if (MC == 16) return run_tc_kernel<10, 16, 0>(a, grid, smem, st);
     return run_tc_kernel<10, 32, 0>(a, grid, smem, st);

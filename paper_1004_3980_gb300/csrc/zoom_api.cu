@@ -473,6 +473,7 @@ struct QueryBufs {
 struct SearchPlan {
   bool tc = false;
   bool capped = false;   // the index caps the candidate set (Sec. 4.2 early stop)
+  int tail_split = 0;     // > 0: whole pairs, then the last round's pairs cut in parts
   int prec = 0, MC = 16, nsplit = 1, KCH = 80;
   int64_t q_rows = 0;
   size_t bytes = 0;
@@ -505,7 +506,26 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   // measured at about kRestartTiles dictionary tiles.
   constexpr int64_t kRestartTiles = 768;
   int64_t nsplit = nsplit_override;
-  if (nsplit <= 0) {
+  if (nsplit <= 0 && nq_pairs >= d->ctx->n_sm) {
+    // whole pairs in step over all SMs (every CTA streams the dictionary from
+    // tile 0 together, so L2 serves it), then the pairs of the last, partial
+    // round cut into S dictionary parts so that it ends sooner: S minimises
+    // the tail's rounds * (tiles per part + list restart)
+    const int64_t grid = d->ctx->n_sm;
+    const int64_t tail = nq_pairs % grid;
+    int64_t best = INT64_MAX;
+    nsplit = 1;
+    for (int64_t sp = 1; tail > 0 && sp <= std::min<int64_t>(8, nd_tiles); ++sp) {
+      const int64_t tps = (nd_tiles + sp - 1) / sp;
+      if ((sp - 1) * tps >= nd_tiles) continue;
+      const int64_t cost = (tail * sp + grid - 1) / grid * (tps + kRestartTiles);
+      if (cost < best) {
+        best = cost;
+        nsplit = sp;
+      }
+    }
+    p.tail_split = (int)nsplit;
+  } else if (nsplit <= 0) {
     int64_t best_cost = INT64_MAX;
     const int64_t grid = std::max(1, d->ctx->n_sm);
     for (int64_t ns = 1; ns <= std::min<int64_t>(8, nd_tiles); ++ns) {
@@ -563,7 +583,7 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
     e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.MC,
-                      pl.nsplit, ctx->n_sm, ld, li, ctx->d_status, st);
+                      pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,

@@ -131,9 +131,12 @@ cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_
                            int precision, uint16_t* op, float* norm_out, cudaStream_t st);
 size_t tc_smem_bytes(int precision);
 int tc_list_size(int precision, int K, int rerank_mult);
+// tail_split > 0: whole query pairs round robin for the full rounds over the
+// grid, the remaining pairs cut into tail_split dictionary parts (nsplit must
+// equal tail_split); 0: nsplit round-robin splits of every pair
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
-                          int64_t nd, int precision, int MC, int nsplit, int grid, float* out_d,
-                          int32_t* out_id, unsigned int* status, cudaStream_t st);
+                          int64_t nd, int precision, int MC, int nsplit, int tail_split, int grid,
+                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st);
 // ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
 // chunk index), ascending; exact = 1 for the FP16-split filter (proof and
 // fallback flags), 0 for the BF16 filter.
