@@ -40,25 +40,38 @@ __global__ void k_bucket_lookup(const uint64_t* __restrict__ qkeys, int64_t nq, 
                                 const int32_t* __restrict__ nuniq, int64_t N,
                                 int32_t* __restrict__ bucket_sum,
                                 unsigned long long* __restrict__ counters) {
-  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nq) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   long long tot = 0;
-  for (int l = 0; l < L; ++l) {
-    const uint64_t key = qkeys[q * L + l];
-    const uint64_t* uk = ukeys + (int64_t)l * N;
-    int lo = 0, hi = nuniq[l];
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (uk[mid] < key) lo = mid + 1; else hi = mid;
+  if (q < nq) {
+    for (int l = 0; l < L; ++l) {
+      const uint64_t key = qkeys[q * L + l];
+      const uint64_t* uk = ukeys + (int64_t)l * N;
+      int lo = 0, hi = nuniq[l];
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (uk[mid] < key) lo = mid + 1; else hi = mid;
+      }
+      if (lo < nuniq[l] && uk[lo] == key) {
+        const int32_t* of = offs + (int64_t)l * (N + 1);
+        tot += of[lo + 1] - of[lo];
+      }
     }
-    if (lo < nuniq[l] && uk[lo] == key) {
-      const int32_t* of = offs + (int64_t)l * (N + 1);
-      tot += of[lo + 1] - of[lo];
-    }
+    if (bucket_sum) bucket_sum[q] = (int32_t)tot;
   }
-  if (bucket_sum) bucket_sum[q] = (int32_t)tot;
-  atomicAdd(&counters[CNT_BUCKET_SUM], (unsigned long long)tot);
-  atomicMax(&counters[CNT_BUCKET_MAX], (unsigned long long)tot);
+  // one atomic per warp (a per-query atomic on one address serialised the
+  // kernel): a query's sum is below L * 2^30, a warp's sum below 2^64
+  const unsigned long long s = (unsigned long long)tot;
+  unsigned long long ws = s, wm = s;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    ws += __shfl_xor_sync(0xffffffffu, ws, off);
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, wm, off);
+    wm = o > wm ? o : wm;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&counters[CNT_BUCKET_SUM], ws);
+    atomicMax(&counters[CNT_BUCKET_MAX], wm);
+  }
 }
 
 // ---------------------------------------------------------------------------
