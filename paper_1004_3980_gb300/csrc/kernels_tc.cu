@@ -736,8 +736,20 @@ __device__ __forceinline__ void warp_merge_best(float& bd, int& bi, float v, int
   bi = ai;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kRerankWarps = 4;   // queries per block
+
 template <int D, int MC>
-__global__ __launch_bounds__(256) void k_rerank(
+__global__ __launch_bounds__(kRerankWarps * 32, 8) void k_rerank(
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
     const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
     const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
@@ -745,9 +757,12 @@ __global__ __launch_bounds__(256) void k_rerank(
     int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ fb_list,
     unsigned long long* __restrict__ counters) {
   constexpr int kDP = (D + 3) / 4 * 4;   // feature row stride (floats)
-  __shared__ float4 s_rows[8][32 * kDP / 4];
+  constexpr int kRow4 = kDP / 4;         // 16-byte pieces per row
+  // two buffers per warp: the next chunk's rows arrive (cp.async) while the
+  // current chunk is examined
+  __shared__ float4 s_rows[kRerankWarps][2][32 * kRow4];
   const int lane = threadIdx.x & 31;
-  float4* srow = s_rows[threadIdx.x >> 5];
+  const int wib = threadIdx.x >> 5;
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (q >= nq) return;   // warp-uniform
   float qv[D];
@@ -763,15 +778,11 @@ __global__ __launch_bounds__(256) void k_rerank(
   float T = lister ? lm[lbase + MC - 1] : FLT_MAX;
 #pragma unroll
   for (int off = 16; off; off >>= 1) T = fminf(T, __shfl_xor_sync(kFull, T, off));
-  // the K best members so far, ascending by (distance, ID): lane j < K holds rank j
-  float bd = FLT_MAX;
-  int bi = INT_MAX;
-  float dK = FLT_MAX, delta = 0.f;
-  int iK = INT_MAX, members = 0;
-  while (true) {
-    // the listed chunk with the smallest minimum (ties: lower split)
-    float best = hv;
-    int bs = lane;
+  // the listed chunk with the smallest minimum among the list heads (ties:
+  // lower split) and its index; -1 when the lists are exhausted
+  auto peek = [&](float& best, int& bs) -> int {
+    best = hv;
+    bs = lane;
     if (nsplit == 1) {
       best = __shfl_sync(kFull, hv, 0);
       bs = 0;
@@ -786,28 +797,59 @@ __global__ __launch_bounds__(256) void k_rerank(
         }
       }
     }
-    if (best == FLT_MAX) break;
-    if (members >= K && best - delta > dK) break;
-    const int chunk = __shfl_sync(kFull, lane == bs ? lc[lbase + head] : 0, bs);
+    if (best == FLT_MAX) return -1;
+    return __shfl_sync(kFull, lane == bs ? lc[lbase + head] : 0, bs);
+  };
+  auto advance = [&](int bs) {
     if (lane == bs) {
       ++head;
       hv = head < MC ? lm[lbase + head] : FLT_MAX;
     }
+  };
+  // the chunk's rows are contiguous: 16-byte asynchronous copies
+  auto stage = [&](int c, int b) {
+    if (c >= 0) {
+      const int64_t e0 = (int64_t)c * 32;
+      const int nrows = nd - e0 < 32 ? (int)(nd - e0) : 32;
+      const float4* g = reinterpret_cast<const float4*>(dfeat + e0 * kDP);
+      float4* dst = s_rows[wib][b];
+      for (int f = lane; f < nrows * kRow4; f += 32) cp_async16(dst + f, g + f);
+    }
+    cp_async_commit();
+  };
+  // the K best members so far, ascending by (distance, ID): lane j < K holds rank j
+  float bd = FLT_MAX;
+  int bi = INT_MAX;
+  float dK = FLT_MAX, delta = 0.f;
+  int iK = INT_MAX, members = 0;
+  float best;
+  int bs;
+  int chunk = peek(best, bs);
+  int buf = 0;
+  if (chunk >= 0) {
+    advance(bs);
+    stage(chunk, 0);
+  }
+  while (chunk >= 0) {
+    // the next chunk in order starts arriving in the other buffer, which held
+    // the previous chunk: the __syncwarp puts every lane past its reads
+    float nbest;
+    int nbs;
+    const int nchunk = peek(nbest, nbs);
+    __syncwarp();
+    stage(nchunk, buf ^ 1);
+    cp_async_wait<1>();   // this lane's copies of the current chunk are done
+    __syncwarp();         // ... and every lane's
     const int64_t e0 = (int64_t)chunk * 32;
     const int64_t e = e0 + lane;
-    // the chunk's 32 feature rows are contiguous: staged through shared
-    // memory with 16-byte loads, then each lane reads its own row
-    const int nrows = chunk < 0 ? 0 : (nd - e0 < 32 ? (int)(nd - e0) : 32);
-    const float4* g = reinterpret_cast<const float4*>(dfeat + e0 * kDP);
-    __syncwarp();   // the previous chunk's rows have been read
-    for (int f = lane; f < nrows * (kDP / 4); f += 32) srow[f] = g[f];
-    __syncwarp();
+    const int nrows = nd - e0 < 32 ? (int)(nd - e0) : 32;
     float dd = FLT_MAX;
     if (lane < nrows) {
+      const float4* srow = s_rows[wib][buf];
       float x[kDP];
 #pragma unroll
-      for (int k = 0; k < kDP / 4; ++k) {
-        const float4 v4 = srow[lane * (kDP / 4) + k];
+      for (int k = 0; k < kRow4; ++k) {
+        const float4 v4 = srow[lane * kRow4 + k];
         x[4 * k] = v4.x;
         x[4 * k + 1] = v4.y;
         x[4 * k + 2] = v4.z;
@@ -876,7 +918,13 @@ __global__ __launch_bounds__(256) void k_rerank(
       const float rc = qnorm + sqrtf(dK) * 1.001f + 1e-6f;
       delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + 4e-6f * dK + 1e-12f;
     }
+    // stop once no entry of a further chunk can beat the K-th member
+    if (nchunk < 0 || (members >= K && nbest - delta > dK)) break;
+    advance(nbs);
+    chunk = nchunk;
+    buf ^= 1;
   }
+  cp_async_wait<0>();   // no copy may still target this warp's buffers
   const bool flagged = members < K || (exact && !(T - delta > dK));
   if (flagged) {
     if (lane == 0) {
@@ -979,8 +1027,8 @@ static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn
                             int tmin, const float* ld, const int32_t* li, int nsplit, int exact, float c_qr,
                             float c_sq, int32_t* nbr, float* dist, int32_t* fb,
                             unsigned long long* counters, cudaStream_t st) {
-  const int64_t blocks = (nq + 7) / 8;   // one warp per query
-  k_rerank<D, MC><<<(unsigned)blocks, 256, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
+  const int64_t blocks = (nq + kRerankWarps - 1) / kRerankWarps;   // one warp per query
+  k_rerank<D, MC><<<(unsigned)blocks, kRerankWarps * 32, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
                                                     li, nsplit, K, exact, c_qr, c_sq, nbr, dist, fb, counters);
   return cudaGetLastError();
 }
