@@ -593,4 +593,13 @@ def gaussian_collision_probability(c: float, w: float) -> float:
     return 1.0 - 2.0 * phi - 2.0 / (math.sqrt(2.0 * math.pi) * r) * (1.0 - math.exp(-r * r / 2.0))
 
 
+def cauchy_collision_probability(c: float, w: float) -> float:
+    """Probability that two points at l1 distance c share one Cauchy-projection
+    hash value floor((a.v + b)/w), b ~ U[0, w) (the 1-stable case of the
+    p-stable scheme the paper cites for its Cauchy projections, Eq. 11):
+    p(c) = 2 atan(w/c) / pi - ln(1 + (w/c)^2) / (pi w/c)."""
+    r = w / c
+    return 2.0 * math.atan(r) / math.pi - math.log1p(r * r) / (math.pi * r)
+
+
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -71,6 +71,30 @@ def test_collision_rate_follows_pstable_law(ratio):
     assert abs(freq - p) < 5 * math.sqrt(p * (1 - p) / n) + 1e-3
 
 
+@pytest.mark.parametrize("ratio", [0.5, 1.0, 2.0, 4.0])
+def test_cauchy_collision_rate_follows_1stable_law(ratio):
+    # Eq. 11 draws alpha_i = a / b (a, b ~ N(0, 1), |b| >= eps): Cauchy
+    # projections, under which two points at l1 distance c collide with the
+    # 1-stable probability p(c) (Datar et al.).  The |b| >= eps rejection
+    # only removes projections beyond 1/eps, immaterial at this sample size.
+    import synth_inputs as S
+    d, w = 6, 1.0
+    c = w / ratio
+    n = 40000
+    alpha, beta = S.lsh_draws_cauchy(int(ratio * 100) + 7, n, 1, d, w)
+    g = np.random.default_rng(int(ratio * 100) + 1)
+    u = g.normal(size=d)
+    u /= np.abs(u).sum()                      # unit l1 norm
+    a = g.normal(size=d)
+    pts = np.stack([a, a + c * u])
+    h, _ = O.hash_values(pts, alpha, beta, w)
+    freq = np.mean(h[0] == h[1])
+    p = O.cauchy_collision_probability(c, w)
+    assert abs(freq - p) < 5 * math.sqrt(p * (1 - p) / n) + 1e-3
+    # and it differs from the Gaussian law at the same l2 distance
+    assert abs(O.gaussian_collision_probability(np.linalg.norm(c * u), w) - p) > 0.01
+
+
 def test_fold_keys_equal_iff_tuples_equal(rng):
     L, k = 3, 4
     base = rng.integers(-3, 3, size=(30, L * k))
