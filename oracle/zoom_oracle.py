@@ -102,21 +102,50 @@ def patch_origins(h: int, w: int, P: int):
     return ii.ravel(), jj.ravel()
 
 
-def patch_features(img: np.ndarray, P: int):
-    """Feature of every overlapping P x P patch: the row-major pixel vector
-    minus its mean (the mean-subtracted raw patch), and the mean mu.
+def gradient_images(img: np.ndarray):
+    """First-order gradients of an image (Sec. 4.1, "Feature representation":
+    convolution with [-1, 0, 1] and its transpose), as the central differences
+    g_x(r, c) = x(r, c+1) - x(r, c-1), g_y(r, c) = x(r+1, c) - x(r-1, c).
+    Readings: borders clamp to the edge (as the blur); the sign is that of
+    the correlation with [-1, 0, 1] (a sign flip changes no distance)."""
+    x = np.asarray(img, dtype=np.float64)
+    h, w = x.shape
+    cm, cp = np.maximum(np.arange(w) - 1, 0), np.minimum(np.arange(w) + 1, w - 1)
+    rm, rp = np.maximum(np.arange(h) - 1, 0), np.minimum(np.arange(h) + 1, h - 1)
+    return x[:, cp] - x[:, cm], x[rp, :] - x[rm, :]
 
-    Sec. 4.1 ("Feature representation") hashes a feature of the LR patch; the
-    feature used here is the mean-subtracted patch."""
+
+# Feature modes of a dictionary (Sec. 4.1): 0 = the LR patch minus its mean
+# (P*P values); 1 = the first-order gradients of the LR image at the patch's
+# pixels (g_x row-major, then g_y: 2*P*P values).
+FEATURE_DIMS = {0: lambda P: P * P, 1: lambda P: 2 * P * P}
+
+
+def patch_features(img: np.ndarray, P: int, feature: int = 0):
+    """Feature of every overlapping P x P patch and its pixel mean mu.
+
+    Sec. 4.1 ("Feature representation") hashes a feature of the LR patch:
+    feature 0 is the mean-subtracted patch, feature 1 the first-order
+    gradients of the image at the patch's pixels (``gradient_images``)."""
     x = np.asarray(img, dtype=np.float64)
     ii, jj = patch_origins(x.shape[0], x.shape[1], P)
     n = len(ii)
-    v = np.empty((n, P * P))
+    px = np.empty((n, P * P))
     for a in range(P):
         for b in range(P):
-            v[:, a * P + b] = x[ii + a, jj + b]
-    mu = v.mean(axis=1)
-    return v - mu[:, None], mu
+            px[:, a * P + b] = x[ii + a, jj + b]
+    mu = px.mean(axis=1)
+    if feature == 0:
+        return px - mu[:, None], mu
+    if feature != 1:
+        raise ValueError("feature must be 0 or 1")
+    gx, gy = gradient_images(x)
+    v = np.empty((n, 2 * P * P))
+    for a in range(P):
+        for b in range(P):
+            v[:, a * P + b] = gx[ii + a, jj + b]
+            v[:, P * P + a * P + b] = gy[ii + a, jj + b]
+    return v, mu
 
 
 @dataclasses.dataclass
@@ -124,7 +153,8 @@ class Dictionary:
     """N LR/HR patch pairs with integer IDs 0..N-1 (Sec. 2.1).
 
     lr_pix  float32 [N][P*P]   stored LR patch pixels
-    feat    float64 [N][P*P]   LR feature (pixels minus mean)
+    feat    float64 [N][D]     LR feature (D = P*P pixels minus mean, or
+                               D = 2*P*P gradients: see patch_features)
     mu      float64 [N]        LR patch mean
     hr_res  float64 [N][PH*PH] HR patch minus the LR patch mean
     """
@@ -134,6 +164,7 @@ class Dictionary:
     feat: np.ndarray
     mu: np.ndarray
     hr_res: np.ndarray
+    feature: int = 0      # feature mode (see patch_features)
 
     @property
     def n(self) -> int:
@@ -144,7 +175,7 @@ class Dictionary:
         return self.scale * self.patch
 
 
-def build_dictionary(hr_images, positions, s: int, P: int, sigma: float) -> Dictionary:
+def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature: int = 0) -> Dictionary:
     """Training pairs (Sec. 2.1, Sec. 5.1): every HR training image is blurred
     and down-sampled; at each position (image, i, j) the LR patch at (i, j) is
     paired with the HR patch of side s*P at (s*i, s*j).
@@ -152,7 +183,8 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float) -> Dict
     Readings: the LR training image is stored at float32, the precision of the
     test LR image; the LR patch mean is subtracted from both patches and is
     added back at reconstruction time.  Position k in ``positions`` (sorted by
-    image, row, column) is the unique ID k."""
+    image, row, column) is the unique ID k.  Feature 1: the gradients of the
+    whole (float32) LR training image at the patch's pixels."""
     lr_imgs = [degrade(np.asarray(x, np.float64), s, sigma).astype(np.float32) for x in hr_images]
     PH = s * P
     N = len(positions)
@@ -163,10 +195,19 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float) -> Dict
         hr[n] = np.asarray(hr_images[m], np.float64)[s * i:s * i + PH, s * j:s * j + PH].ravel()
     lr64 = lr_pix.astype(np.float64)
     mu = lr64.mean(axis=1)
-    return Dictionary(s, P, lr_pix, lr64 - mu[:, None], mu, hr - mu[:, None])
+    if feature == 0:
+        feat = lr64 - mu[:, None]
+    else:
+        grads = [gradient_images(x) for x in lr_imgs]
+        feat = np.empty((N, 2 * P * P))
+        for n, (m, i, j) in enumerate(np.asarray(positions)):
+            gx, gy = grads[m]
+            feat[n, :P * P] = gx[i:i + P, j:j + P].ravel()
+            feat[n, P * P:] = gy[i:i + P, j:j + P].ravel()
+    return Dictionary(s, P, lr_pix, feat, mu, hr - mu[:, None], feature)
 
 
-def dictionary_from_lr_hr(lr_img, hr_img, s: int, P: int) -> Dictionary:
+def dictionary_from_lr_hr(lr_img, hr_img, s: int, P: int, feature: int = 0) -> Dictionary:
     """Every patch pair of one given LR/HR image pair (used for the
     exact-reconstruction pins: the test image's own patches in the dictionary,
     as in the girl-image experiment of Sec. 5.2)."""
@@ -176,9 +217,8 @@ def dictionary_from_lr_hr(lr_img, hr_img, s: int, P: int) -> Dictionary:
     PH = s * P
     lr_pix = np.stack([lr[i:i + P, j:j + P].ravel() for i, j in zip(ii, jj)])
     hrp = np.stack([hr[s * i:s * i + PH, s * j:s * j + PH].ravel() for i, j in zip(ii, jj)])
-    lr64 = lr_pix.astype(np.float64)
-    mu = lr64.mean(axis=1)
-    return Dictionary(s, P, lr_pix, lr64 - mu[:, None], mu, hrp - mu[:, None])
+    feat, mu = patch_features(lr, P, feature)
+    return Dictionary(s, P, lr_pix, feat, mu, hrp - mu[:, None], feature)
 
 
 # ---------------------------------------------------------------------------
@@ -464,7 +504,7 @@ def query(lr: np.ndarray, d: Dictionary, index: LshIndex, K: int, reg_rel: float
     """Per-patch inference of Sec. 4.2 for the queries numbered ``rows``
     (default: all, row order): hash, collect the candidates, K nearest,
     LLE weights."""
-    v, mu = patch_features(lr, d.patch)
+    v, mu = patch_features(lr, d.patch, d.feature)
     if rows is None:
         rows = np.arange(v.shape[0])
     rows = np.asarray(rows)

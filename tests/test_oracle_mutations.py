@@ -8,6 +8,7 @@ import pytest
 from oracle import zoom_oracle as O
 from tests import test_golden as TG
 from tests import test_oracle_degrade as TD
+from tests import test_oracle_features as TF
 from tests import test_oracle_hash as TH
 from tests import test_oracle_knn_lle as TK
 from tests import test_oracle_recon_bp as TR
@@ -107,3 +108,29 @@ def test_missing_prior_factor_is_caught(monkeypatch):
     orig = O.overlap_prior_grad
     monkeypatch.setattr(O, "overlap_prior_grad", lambda p, h, w, s, P: 0.5 * orig(p, h, w, s, P))
     _fails(TR.test_prior_gradient_matches_central_differences)
+
+
+def test_gradient_with_wrapped_borders_is_caught(monkeypatch):
+    # periodic instead of clamped borders
+    def grad_wrap(img):
+        x = np.asarray(img, np.float64)
+        return np.roll(x, -1, axis=1) - np.roll(x, 1, axis=1), np.roll(x, -1, axis=0) - np.roll(x, 1, axis=0)
+    monkeypatch.setattr(O, "gradient_images", grad_wrap)
+    _fails(TF.test_gradient_feature_layout_brute_force, np.random.default_rng(0), 3)
+
+
+def test_one_sided_gradient_is_caught(monkeypatch):
+    # forward differences x(c+1) - x(c) in place of the centred [-1, 0, 1]
+    def grad_fwd(img):
+        x = np.asarray(img, np.float64)
+        gx = np.concatenate([x[:, 1:] - x[:, :-1], np.zeros((x.shape[0], 1))], axis=1)
+        gy = np.concatenate([x[1:] - x[:-1], np.zeros((1, x.shape[1]))], axis=0)
+        return gx, gy
+    monkeypatch.setattr(O, "gradient_images", grad_fwd)
+    _fails(TF.test_gradients_of_a_ramp)
+
+
+def test_swapped_gradient_halves_are_caught(monkeypatch):
+    orig = O.gradient_images
+    monkeypatch.setattr(O, "gradient_images", lambda img: orig(img)[::-1])
+    _fails(TF.test_gradient_feature_layout_brute_force, np.random.default_rng(0), 5)
