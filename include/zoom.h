@@ -63,13 +63,21 @@ typedef struct {
  * sigma blur_sigma, clamped borders) -> s x s box down-sampling.  LR patches
  * are lr_patch x lr_patch; HR patches are (scale*lr_patch)^2.  blur_sigma is
  * a double so that the taps are computed from the exact parameter value.
- * Supported: scale 1..4, blur_sigma > 0; dictionaries and queries need
- * lr_patch 3 or 5 (UNSUPPORTED otherwise); the image-only calls
- * (zoom_backproject, zoom_degrade, their adjoints) ignore lr_patch. */
+ * feature selects the feature an LR patch is hashed and matched by (Sec.
+ * 4.1, "Feature representation"): 0 = the P*P pixels minus their mean;
+ * 1 = the first-order gradients of the LR image at the patch's pixels,
+ * g_x(r,c) = x(r,c+1) - x(r,c-1) then g_y(r,c) = x(r+1,c) - x(r-1,c), each
+ * row-major over the patch, image coordinates clamped to the image (2*P*P
+ * values).  Either way the HR patch is stored and blended relative to the LR
+ * patch mean.  Supported: scale 1..4, blur_sigma > 0, feature 0 or 1;
+ * dictionaries and queries need lr_patch 3 or 5 (UNSUPPORTED otherwise); the
+ * image-only calls (zoom_backproject, zoom_degrade, their adjoints) ignore
+ * lr_patch and feature. */
 typedef struct {
   int32_t scale;
   int32_t lr_patch;
   double blur_sigma;
+  int32_t feature;
 } zoom_degradation;
 
 /* LSH parameters (Sec. 3.2, Sec. 4.1).  L tables of k concatenated hashes
@@ -155,9 +163,10 @@ const char* zoom_last_error(void);
  * LR row i, LR col j) (host int32 [n_pairs][3]): LR patch at (i, j) and HR
  * patch at (s*i, s*j).  Pair n gets ID n; positions should be sorted by
  * (m, i, j) so that IDs follow the paper's row order.  Stored per pair:
- * the LR pixels, the LR mean mu, the feature (pixels - mu) and the HR patch
- * minus mu.  Errors: INVALID_ARG for sizes out of range or positions whose
- * patch leaves its image (checked on the host). */
+ * the LR pixels, the LR mean mu, the feature (degr->feature; gradients are
+ * taken on the whole LR training image) and the HR patch minus mu.  Errors:
+ * INVALID_ARG for sizes out of range or positions whose patch leaves its
+ * image (checked on the host). */
 zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
                                   const int32_t* heights, const int32_t* widths,
                                   int32_t n_images, const zoom_degradation* degr,
@@ -167,13 +176,15 @@ void zoom_dict_destroy(zoom_dict d);
 /* Copies stored arrays to the host (synchronises `stream`): lr_pix [N][P*P],
  * mu [N], hr_res [N][(s*P)^2]; any pointer may be NULL. */
 zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_res, void* stream);
-/* Dictionary sizes: N, LR patch side P, scale s, and the blur sigma of its
- * degradation; any pointer may be NULL. */
-zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma);
+/* Dictionary sizes: N, LR patch side P, scale s, the blur sigma of its
+ * degradation, its feature mode and feature dimension D (P*P or 2*P*P); any
+ * pointer may be NULL. */
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma,
+                           int32_t* feature, int32_t* feature_dim);
 
 /* ---- LSH index (Sec. 3.2; Sec. 4.1, Eq. 10) -----------------------------
  * Hashes every dictionary feature into L tables.  alpha: host float32
- * [L*k][P*P] projection vectors; beta: host float32 [L*k] offsets in
+ * [L*k][D] projection vectors (D the feature dimension); beta: host float32 [L*k] offsets in
  * [0, w) (the random draws are inputs).  Builds, per table, the bucket key
  * of every entry and a CSR of its bins (keys radix-sorted on the device).
  * Errors: INVALID_ARG for parameters out of range. */
@@ -191,11 +202,11 @@ zoom_status zoom_index_info(zoom_index ix, zoom_lsh_params* lsh);
  * The paper keeps the N training pairs on disk once extracted (Sec. 2.1).
  * zoom_dict_save writes every array the dictionary stores (LR pixels, the
  * features, mu, squared feature norms and the HR residuals, float32) after a
- * little-endian header ("ZOOMDICT", version 1, N, P, s, blur_sigma and the
- * row strides); zoom_dict_load reads such a file into a new dictionary on
- * ctx, bit-identical to the saved one.  zoom_index_save writes the LSH
- * parameters and the projections ("ZOOMINDX", version 1, N, P*P, L, k,
- * min_table_hits, max_candidates, w; then alpha [L*k][P*P], beta [L*k]);
+ * little-endian header ("ZOOMDICT", version 1, the feature mode, N, P, s,
+ * blur_sigma and the row strides); zoom_dict_load reads such a file into a
+ * new dictionary on ctx, bit-identical to the saved one.  zoom_index_save
+ * writes the LSH parameters and the projections ("ZOOMINDX", version 1, N,
+ * D, L, k, min_table_hits, max_candidates, w; then alpha [L*k][D], beta [L*k]);
  * zoom_index_load rebuilds the index on dictionary d from them (the same
  * keys and bins as the saved index).  All four synchronise `stream`; the
  * caller owns `path` (a NUL-terminated file name).  Errors: IO (cannot
@@ -207,7 +218,7 @@ zoom_status zoom_dict_load(zoom_ctx ctx, const char* path, void* stream, zoom_di
 zoom_status zoom_index_save(zoom_index ix, const char* path, void* stream);
 zoom_status zoom_index_load(zoom_dict d, const char* path, void* stream, zoom_index* out);
 /* Copies the index's random draws to the host (synchronises `stream`):
- * alpha float32 [L*k][P*P], beta float32 [L*k] (Eq. 10); either may be NULL. */
+ * alpha float32 [L*k][D], beta float32 [L*k] (Eq. 10); either may be NULL. */
 zoom_status zoom_export_params(zoom_index ix, float* alpha, float* beta, void* stream);
 
 /* ---- inference ------------------------------------------------------------

@@ -26,6 +26,7 @@ SOURCES = [
     "zoom_api.cu",
     "kernels_build.cu",
     "kernels_query.cu",
+    "kernels_query_grad.cu",
     "kernels_image.cu",
     "kernels_tc.cu",
     "zoom_noalloc.cu",
@@ -33,7 +34,7 @@ SOURCES = [
     "zoom_api_backward.cu",
     "zoom_io.cu",
 ]
-HEADERS = ["zoom_internal.h", "device_common.cuh"]
+HEADERS = ["zoom_internal.h", "device_common.cuh", "knn_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,7 +23,8 @@ class Allocator(C.Structure):
 
 
 class Degradation(C.Structure):
-    _fields_ = [("scale", C.c_int32), ("lr_patch", C.c_int32), ("blur_sigma", C.c_double)]
+    _fields_ = [("scale", C.c_int32), ("lr_patch", C.c_int32), ("blur_sigma", C.c_double),
+                ("feature", C.c_int32)]
 
 
 class LshParams(C.Structure):
@@ -59,7 +60,7 @@ SIGNATURES = {
                                         _i64, _P(_i32), _vp, _P(_vp)]),
     "zoom_dict_destroy": (None, [_vp]),
     "zoom_dict_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
-    "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(C.c_double)]),
+    "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(C.c_double), _P(_i32), _P(_i32)]),
     "zoom_dict_save": (C.c_int, [_vp, C.c_char_p, _vp]),
     "zoom_dict_load": (C.c_int, [_vp, C.c_char_p, _vp, _P(_vp)]),
     "zoom_index_save": (C.c_int, [_vp, C.c_char_p, _vp]),

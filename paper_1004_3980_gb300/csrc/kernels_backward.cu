@@ -268,6 +268,8 @@ cudaError_t launch_nbr_dist(const float* qfeat, int dpad, int d, int64_t nq, con
   const unsigned blocks = (unsigned)((tot + 127) / 128);
   if (d == 9) k_nbr_dist<9><<<blocks, 128, 0, st>>>(qfeat, dpad, nq, dfeat, nbr, K, dist);
   else if (d == 25) k_nbr_dist<25><<<blocks, 128, 0, st>>>(qfeat, dpad, nq, dfeat, nbr, K, dist);
+  else if (d == 18) k_nbr_dist<18><<<blocks, 128, 0, st>>>(qfeat, dpad, nq, dfeat, nbr, K, dist);
+  else if (d == 50) k_nbr_dist<50><<<blocks, 128, 0, st>>>(qfeat, dpad, nq, dfeat, nbr, K, dist);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

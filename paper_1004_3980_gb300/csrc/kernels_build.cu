@@ -57,29 +57,36 @@ __global__ void k_degrade_exact(const float* __restrict__ hr, int H, int W, int 
   lr[(size_t)i * w + j] = shi + slo;
 }
 
-template <int P>
+template <int P, int F>
 __global__ void k_dict_gather(const float* const* __restrict__ lr_images,
-                              const int32_t* __restrict__ lr_w,
+                              const int32_t* __restrict__ lr_h, const int32_t* __restrict__ lr_w,
                               const float* const* __restrict__ hr_images,
                               const int32_t* __restrict__ hr_w, const int32_t* __restrict__ pos,
                               int64_t n, int s, int dpad, int ph2pad, float* __restrict__ lr_pix,
                               float* __restrict__ feat, float* __restrict__ mu,
                               float* __restrict__ norm2, float* __restrict__ hr_res) {
-  constexpr int D = P * P;
+  constexpr int P2 = P * P;
+  constexpr int D = zoom_feature_dim(P, F);
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   int m = pos[e * 3 + 0], i = pos[e * 3 + 1], j = pos[e * 3 + 2];
   const float* lr = lr_images[m];
   int lw = lr_w[m];
-  float px[D], v[D], mean, n2;
+  float px[P2], v[P2], mean, n2;
 #pragma unroll
   for (int a = 0; a < P; ++a)
 #pragma unroll
     for (int b = 0; b < P; ++b) px[a * P + b] = lr[(size_t)(i + a) * lw + j + b];
-  zoom_patch_feature<D>(px, v, mean, n2);
+  zoom_patch_feature<P2>(px, v, mean, n2);
 #pragma unroll
-  for (int q = 0; q < D; ++q) lr_pix[e * D + q] = px[q];
-  for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? v[q] : 0.f;
+  for (int q = 0; q < P2; ++q) lr_pix[e * P2 + q] = px[q];
+  if constexpr (F == 0) {
+    for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? v[q] : 0.f;
+  } else {
+    float g[D];
+    zoom_gradient_feature<P>(lr, lr_h[m], lw, (size_t)lw, i, j, g, n2);
+    for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? g[q] : 0.f;
+  }
   mu[e] = mean;
   norm2[e] = n2;
   const float* hr = hr_images[m];
@@ -334,21 +341,21 @@ cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, double si
   return cudaGetLastError();
 }
 
-cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_w,
-                               const float* const* d_hr_images, const int32_t* d_hr_w,
-                               const int32_t* d_pos, int64_t n, int P, int s, zoom_dict d,
-                               cudaStream_t st) {
+cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_h,
+                               const int32_t* d_lr_w, const float* const* d_hr_images,
+                               const int32_t* d_hr_w, const int32_t* d_pos, int64_t n, int P, int s,
+                               zoom_dict d, cudaStream_t st) {
   int blocks = (int)((n + 127) / 128);
-  if (P == 3)
-    k_dict_gather<3><<<blocks, 128, 0, st>>>(d_lr_images, d_lr_w, d_hr_images, d_hr_w, d_pos, n, s,
-                                             d->dpad, d->ph2pad, d->lr_pix, d->feat, d->mu,
-                                             d->norm2, d->hr_res);
-  else if (P == 5)
-    k_dict_gather<5><<<blocks, 128, 0, st>>>(d_lr_images, d_lr_w, d_hr_images, d_hr_w, d_pos, n, s,
-                                             d->dpad, d->ph2pad, d->lr_pix, d->feat, d->mu,
-                                             d->norm2, d->hr_res);
-  else
-    return cudaErrorInvalidValue;
+#define ZOOM_GATHER(PP, FF)                                                                     \
+  k_dict_gather<PP, FF><<<blocks, 128, 0, st>>>(d_lr_images, d_lr_h, d_lr_w, d_hr_images, d_hr_w, \
+                                                d_pos, n, s, d->dpad, d->ph2pad, d->lr_pix,      \
+                                                d->feat, d->mu, d->norm2, d->hr_res)
+  if (P == 3 && d->feature == 0) ZOOM_GATHER(3, 0);
+  else if (P == 5 && d->feature == 0) ZOOM_GATHER(5, 0);
+  else if (P == 3 && d->feature == 1) ZOOM_GATHER(3, 1);
+  else if (P == 5 && d->feature == 1) ZOOM_GATHER(5, 1);
+  else return cudaErrorInvalidValue;
+#undef ZOOM_GATHER
   return cudaGetLastError();
 }
 
@@ -357,17 +364,20 @@ cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const flo
   if (n == 0) return cudaSuccess;
   size_t smem = (size_t)L * k * (d + 1) * sizeof(float);
   int blocks = (int)((n + 127) / 128);
-  if (d == 9) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_hash<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hash<9><<<blocks, 128, smem, st>>>(feat, dpad, n, alpha, beta, L, k, w, keys);
-  } else if (d == 25) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_hash<25>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hash<25><<<blocks, 128, smem, st>>>(feat, dpad, n, alpha, beta, L, k, w, keys);
-  } else {
-    return cudaErrorInvalidValue;
+#define ZOOM_HASH(DD)                                                                       \
+  do {                                                                                      \
+    if (smem > 48 * 1024)                                                                   \
+      cudaFuncSetAttribute(k_hash<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_hash<DD><<<blocks, 128, smem, st>>>(feat, dpad, n, alpha, beta, L, k, w, keys);        \
+  } while (0)
+  switch (d) {
+    case 9: ZOOM_HASH(9); break;
+    case 25: ZOOM_HASH(25); break;
+    case 18: ZOOM_HASH(18); break;
+    case 50: ZOOM_HASH(50); break;
+    default: return cudaErrorInvalidValue;
   }
+#undef ZOOM_HASH
   return cudaGetLastError();
 }
 

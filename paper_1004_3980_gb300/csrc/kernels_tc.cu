@@ -42,11 +42,25 @@ namespace {
 // one per query tile; 11 warps, 168 registers).
 __host__ __device__ constexpr int tc_mma_warps(int MC) { return MC <= 16 ? 4 : 2; }
 __host__ __device__ constexpr int tc_threads(int MC) { return (9 + tc_mma_warps(MC)) * 32; }
-// Dictionary-tile ring depth: enough bulk copies in flight to cover their
-// latency, within the shared memory left by the query tiles and the buffers.
-__host__ __device__ constexpr int tc_stages(int KC) { return KC >= 10 ? 7 : 16; }
 constexpr int kBarBytes = 512;
 constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
+// Per epilogue lane, chunks below the threshold are first appended to a
+// shared-memory buffer of kBuf slots (a few instructions each) and merged
+// into the sorted register list when some lane of the warp runs out of room:
+// the merge loop then runs for all lanes together, so the sorted insertions
+// execute with the warp converged.
+constexpr int kBuf = 16;
+constexpr int kSmemMax = 232448;  // shared memory a CTA may opt into (227 KB)
+// Dictionary-tile ring depth: as many bulk copies in flight as the shared
+// memory left by the two query tiles, the barriers and the append buffers
+// holds, up to 16 (KC = 4: 16, 8: 10, 10: 7, 20: 2).
+__host__ __device__ constexpr int tc_stages(int KC) {
+  return (kSmemMax - 1024 - kBarBytes - kBuf * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16) < 16
+             ? (kSmemMax - 1024 - kBarBytes - kBuf * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16)
+             : 16;
+}
+static_assert(tc_stages(4) == 16 && tc_stages(8) == 10 && tc_stages(10) == 7 && tc_stages(20) == 2,
+              "ring depths");
 constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
 
 // ---------------------------------------------------------------------------
@@ -302,12 +316,6 @@ __device__ __forceinline__ void list_push(float (&ld)[MC], int (&li)[MC], float 
   li[0] = first ? id : li[0];
 }
 
-// Per epilogue lane, chunks below the threshold are first appended to a
-// shared-memory buffer of kBuf slots (a few instructions each) and merged
-// into the sorted register list when some lane of the warp runs out of room:
-// the merge loop then runs for all lanes together, so the sorted insertions
-// execute with the warp converged.
-constexpr int kBuf = 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int MC>
@@ -584,16 +592,18 @@ __device__ __forceinline__ uint16_t b_bits(__nv_bfloat16 h) { return __bfloat16_
 
 // role 0: query rows, role 1: dictionary rows.  Rows in [n, n_rows) are
 // padding: queries get zeros, dictionary entries a huge norm so that they
-// never rank.
-template <int D>
+// never rank.  Exact form: the three D-element groups start at 0, S and 2S
+// and the norm pair sits at 3S (S = 25 for K = 80, 50 for K = 160).
+template <int D, int KC>
 __global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
                                 int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
-  constexpr int KC = 10;
+  constexpr int S = KC * 5 / 2;
+  static_assert(D <= S && 3 * S + 2 <= KC * 8, "operand layout");
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
-  uint16_t row[80];
+  uint16_t row[KC * 8];
 #pragma unroll
-  for (int k = 0; k < 80; ++k) row[k] = 0;
+  for (int k = 0; k < KC * 8; ++k) row[k] = 0;
   if (r < n) {
     float n2 = 0.f;
 #pragma unroll
@@ -604,26 +614,26 @@ __global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_
       const __half lo = __float2half_rn(v - __half2float(hi));
       if (role == 0) {
         row[i] = h_bits(hi);
-        row[25 + i] = h_bits(lo);
-        row[50 + i] = h_bits(hi);
+        row[S + i] = h_bits(lo);
+        row[2 * S + i] = h_bits(hi);
       } else {
         const __half mh = __float2half_rn(-2.f * __half2float(hi));
         row[i] = h_bits(mh);
-        row[25 + i] = h_bits(mh);
-        row[50 + i] = h_bits(__float2half_rn(-2.f * __half2float(lo)));
+        row[S + i] = h_bits(mh);
+        row[2 * S + i] = h_bits(__float2half_rn(-2.f * __half2float(lo)));
       }
     }
     if (role == 0) {
-      row[75] = h_bits(__float2half_rn(1.f));
-      row[76] = h_bits(__float2half_rn(1.f));
+      row[3 * S] = h_bits(__float2half_rn(1.f));
+      row[3 * S + 1] = h_bits(__float2half_rn(1.f));
     } else {
       const __half nh = __float2half_rn(n2);
-      row[75] = h_bits(nh);
-      row[76] = h_bits(__float2half_rn(n2 - __half2float(nh)));
+      row[3 * S] = h_bits(nh);
+      row[3 * S + 1] = h_bits(__float2half_rn(n2 - __half2float(nh)));
     }
     if (norm_out) norm_out[r] = n2;
   } else if (role == 1) {
-    row[75] = h_bits(__float2half_rn(60000.f));
+    row[3 * S] = h_bits(__float2half_rn(60000.f));
   }
 #pragma unroll
   for (int kc = 0; kc < KC; ++kc) {
@@ -636,15 +646,15 @@ __global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_
   }
 }
 
-template <int D>
+template <int D, int KC>
 __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
-  constexpr int KC = 4;
+  static_assert(D + 3 <= KC * 8, "operand layout");
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
-  uint16_t row[32];
+  uint16_t row[KC * 8];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) row[k] = 0;
+  for (int k = 0; k < KC * 8; ++k) row[k] = 0;
   if (r < n) {
     float n2 = 0.f;
 #pragma unroll
@@ -746,10 +756,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-constexpr int kRerankWarps = 4;   // queries per block
+// queries (warps) per block: the staged rows of wide features (D = 50, two
+// buffers of 32 rows of 52 floats per warp) would exceed 48 KB of static
+// shared memory at four warps
+__host__ __device__ constexpr int rerank_warps(int D) { return D > 32 ? 2 : 4; }
 
 template <int D, int MC>
-__global__ __launch_bounds__(kRerankWarps * 32, 8) void k_rerank(
+__global__ __launch_bounds__(rerank_warps(D) * 32, 8) void k_rerank(
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
     const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
     const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
@@ -760,6 +773,9 @@ __global__ __launch_bounds__(kRerankWarps * 32, 8) void k_rerank(
   constexpr int kRow4 = kDP / 4;         // 16-byte pieces per row
   // two buffers per warp: the next chunk's rows arrive (cp.async) while the
   // current chunk is examined
+  constexpr int kRerankWarps = rerank_warps(D);
+  // relative error of the FP32 difference-form distance of D terms
+  constexpr float kRelD = D > 25 ? 8e-6f : 4e-6f;
   __shared__ float4 s_rows[kRerankWarps][2][32 * kRow4];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -846,20 +862,36 @@ __global__ __launch_bounds__(kRerankWarps * 32, 8) void k_rerank(
     float dd = FLT_MAX;
     if (lane < nrows) {
       const float4* srow = s_rows[wib][buf];
-      float x[kDP];
-#pragma unroll
-      for (int k = 0; k < kRow4; ++k) {
-        const float4 v4 = srow[lane * kRow4 + k];
-        x[4 * k] = v4.x;
-        x[4 * k + 1] = v4.y;
-        x[4 * k + 2] = v4.z;
-        x[4 * k + 3] = v4.w;
-      }
       dd = 0.f;
+      if constexpr (D <= 32) {
+        float x[kDP];
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const float df = qv[i] - x[i];
-        dd = fmaf(df, df, dd);
+        for (int k = 0; k < kRow4; ++k) {
+          const float4 v4 = srow[lane * kRow4 + k];
+          x[4 * k] = v4.x;
+          x[4 * k + 1] = v4.y;
+          x[4 * k + 2] = v4.z;
+          x[4 * k + 3] = v4.w;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const float df = qv[i] - x[i];
+          dd = fmaf(df, df, dd);
+        }
+      } else {
+        // wide rows: consume each 16-byte piece as it is read (same order)
+#pragma unroll
+        for (int k = 0; k < kRow4; ++k) {
+          const float4 v4 = srow[lane * kRow4 + k];
+          const float x4[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (4 * k + t < D) {
+              const float df = qv[4 * k + t] - x4[t];
+              dd = fmaf(df, df, dd);
+            }
+          }
+        }
       }
     }
     // entries that could still enter the K best: LSH membership
@@ -916,7 +948,7 @@ __global__ __launch_bounds__(kRerankWarps * 32, 8) void k_rerank(
       iK = __shfl_sync(kFull, bi, K - 1);
       // an entry that could beat dK has ||c|| <= ||q|| + sqrt(dK)
       const float rc = qnorm + sqrtf(dK) * 1.001f + 1e-6f;
-      delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + 4e-6f * dK + 1e-12f;
+      delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + kRelD * dK + 1e-12f;
     }
     // stop once no entry of a further chunk can beat the K-th member
     if (nchunk < 0 || (members >= K && nbest - delta > dK)) break;
@@ -952,27 +984,35 @@ int64_t tc_rows_padded(int64_t n, bool even_tiles) {
   return t * TC_ROWS;
 }
 
+int tc_kc(int d, int precision) {
+  if (precision == 0) return d <= 25 ? 10 : 20;
+  return d + 3 <= 32 ? 4 : 8;
+}
+
 cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
                            int precision, uint16_t* op, float* norm_out, cudaStream_t st) {
   const int blocks = (int)((n_rows + 127) / 128);
-  if (d == 25) {
-    if (precision == 0)
-      k_operand_f16x3<25><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
-    else
-      k_operand_bf16<25><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
-  } else if (d == 9) {
-    if (precision == 0)
-      k_operand_f16x3<9><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
-    else
-      k_operand_bf16<9><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, norm_out);
-  } else {
-    return cudaErrorInvalidValue;
+#define ZOOM_OP(DD)                                                                                  \
+  do {                                                                                               \
+    if (precision == 0)                                                                              \
+      k_operand_f16x3<DD, (DD <= 25 ? 10 : 20)><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, \
+                                                                         norm_out);                  \
+    else                                                                                             \
+      k_operand_bf16<DD, (DD + 3 <= 32 ? 4 : 8)><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, \
+                                                                          norm_out);                 \
+  } while (0)
+  switch (d) {
+    case 9: ZOOM_OP(9); break;
+    case 25: ZOOM_OP(25); break;
+    case 18: ZOOM_OP(18); break;
+    case 50: ZOOM_OP(50); break;
+    default: return cudaErrorInvalidValue;
   }
+#undef ZOOM_OP
   return cudaGetLastError();
 }
 
-size_t tc_smem_bytes(int precision) {
-  const int KC = precision == 0 ? 10 : 4;
+size_t tc_smem_bytes(int KC) {
   // alignment pad + operand tiles + barriers + the epilogue append buffers
   return 1024 + (size_t)(2 + tc_stages(KC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)kBuf * 256 * 8;
 }
@@ -992,7 +1032,7 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
 }
 
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
-                          int64_t nd, int precision, int MC, int nsplit, int tail_split, int grid,
+                          int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
                           float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st) {
   TcArgs a;
   a.qop = qop;
@@ -1009,16 +1049,19 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
   a.status = status;
   a.tail_split = tail_split;
   if (tail_split > 0 && nsplit != tail_split) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(precision);
+  if (MC != 16 && MC != 32) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(kc);
   const int items = tail_split > 0 ? a.nq_pairs : a.nsplit * a.nq_pairs;
   grid = grid < items ? grid : items;
   a.full_rounds = tail_split > 0 ? a.nq_pairs / grid : 0;
-  if (precision == 0) {
-    if (MC == 16) return run_tc_kernel<10, 16, 0>(a, grid, smem, st);
-    return run_tc_kernel<10, 32, 0>(a, grid, smem, st);
-  }
-  if (MC == 16) return run_tc_kernel<4, 16, 1>(a, grid, smem, st);
-  return run_tc_kernel<4, 32, 1>(a, grid, smem, st);
+#define ZOOM_TC(KC, T)                                                                            \
+  return MC == 16 ? run_tc_kernel<KC, 16, T>(a, grid, smem, st) : run_tc_kernel<KC, 32, T>(a, grid, smem, st)
+  if (precision == 0 && kc == 10) ZOOM_TC(10, 0);
+  if (precision == 0 && kc == 20) ZOOM_TC(20, 0);
+  if (precision == 1 && kc == 4) ZOOM_TC(4, 1);
+  if (precision == 1 && kc == 8) ZOOM_TC(8, 1);
+#undef ZOOM_TC
+  return cudaErrorInvalidValue;
 }
 
 template <int D, int MC>
@@ -1027,6 +1070,7 @@ static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn
                             int tmin, const float* ld, const int32_t* li, int nsplit, int exact, float c_qr,
                             float c_sq, int32_t* nbr, float* dist, int32_t* fb,
                             unsigned long long* counters, cudaStream_t st) {
+  constexpr int kRerankWarps = rerank_warps(D);
   const int64_t blocks = (nq + kRerankWarps - 1) / kRerankWarps;   // one warp per query
   k_rerank<D, MC><<<(unsigned)blocks, kRerankWarps * 32, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
                                                     li, nsplit, K, exact, c_qr, c_sq, nbr, dist, fb, counters);
@@ -1046,8 +1090,12 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
   // of 80 terms and the FP32 rerank (2^-16 (r^2 + ||q||^2), 4e-6 d).  BF16
   // form: each operand rounded to 8 significant bits (2 * 2^-8 ||q|| r for
   // the product term), 32 FP32 accumulations; used only to stop examining.
-  const float c_qr = exact ? 6.f / 65536.f : 1.05f / 128.f;
-  const float c_sq = exact ? 1.f / 65536.f : 1.f / 262144.f;
+  // Twice the operand width (gradient features of 5 x 5 patches, K = 160
+  // or 64) doubles the accumulation terms: the coefficients are doubled (the
+  // kernel doubles the relative term of its FP32 rerank for D > 25 too).
+  const float wide = tc_kc(d, exact ? 0 : 1) > (exact ? 10 : 4) ? 2.f : 1.f;
+  const float c_qr = wide * (exact ? 6.f / 65536.f : 1.05f / 128.f);
+  const float c_sq = wide * (exact ? 1.f / 65536.f : 1.f / 262144.f);
 #define ZOOM_RR(DD, MM)                                                                          \
   return rerank_k<DD, MM>(K, qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld, li, nsplit, \
                           exact, c_qr, c_sq, nbr, dist, fb, counters, st)
@@ -1055,6 +1103,10 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
   if (d == 25 && MC == 32) ZOOM_RR(25, 32);
   if (d == 9 && MC == 16) ZOOM_RR(9, 16);
   if (d == 9 && MC == 32) ZOOM_RR(9, 32);
+  if (d == 18 && MC == 16) ZOOM_RR(18, 16);
+  if (d == 18 && MC == 32) ZOOM_RR(18, 32);
+  if (d == 50 && MC == 16) ZOOM_RR(50, 16);
+  if (d == 50 && MC == 32) ZOOM_RR(50, 32);
 #undef ZOOM_RR
   return cudaErrorInvalidValue;
 }

@@ -57,20 +57,22 @@ struct Carver {
 
 }  // namespace
 
-zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, cudaStream_t st) {
+zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, int feature,
+                          cudaStream_t st) {
   zoom_dict d = new zoom_dict_s();
   d->ctx = ctx;
   d->n = n;
   d->P = P;
   d->s = s;
-  d->d = P * P;
+  d->feature = feature;
+  d->d = feature ? 2 * P * P : P * P;
   d->dpad = (d->d + 3) / 4 * 4;
   d->PH = s * P;
   d->ph2 = d->PH * d->PH;
   d->ph2pad = (d->ph2 + 3) / 4 * 4;
   d->blur_sigma = blur_sigma;
   Carver c0(nullptr);
-  c0.take<float>(n * d->d);
+  c0.take<float>(n * P * P);
   c0.take<float>(n * d->dpad);
   c0.take<float>(n);
   c0.take<float>(n);
@@ -82,7 +84,7 @@ zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sig
     return nullptr;
   }
   Carver c(mem);
-  d->lr_pix = c.take<float>(n * d->d);   // first: the allocation's base
+  d->lr_pix = c.take<float>(n * P * P);   // first: the allocation's base
   d->feat = c.take<float>(n * d->dpad);
   d->mu = c.take<float>(n);
   d->norm2 = c.take<float>(n);
@@ -107,7 +109,6 @@ bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string
     why = "rerank_mult * K must be in K..32"; return false;
   }
   if (p->search < 0 || p->search > 2) { why = "search must be 0, 1 or 2"; return false; }
-  if (p->precision == 1 && (d->d != 9 && d->d != 25)) { why = "unsupported patch size"; return false; }
   return true;
 }
 
@@ -217,6 +218,7 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   if (s < 1 || s > 4) return fail(ZOOM_ERR_INVALID_ARG, "scale must be in 1..4");
   if (P != 3 && P != 5) return fail(ZOOM_ERR_UNSUPPORTED, "lr_patch must be 3 or 5");
   if (!(degr->blur_sigma > 0.f)) return fail(ZOOM_ERR_INVALID_ARG, "blur_sigma must be > 0");
+  if (degr->feature != 0 && degr->feature != 1) return fail(ZOOM_ERR_INVALID_ARG, "feature must be 0 or 1");
   if (n_images < 1 || n_pairs < 1 || n_pairs > (1LL << 30))
     return fail(ZOOM_ERR_INVALID_ARG, "n_images and n_pairs must be positive");
   for (int m = 0; m < n_images; ++m) {
@@ -232,7 +234,7 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   }
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(ctx->device));
-  zoom_dict d = zoom_dict_alloc(ctx, n_pairs, P, s, degr->blur_sigma, st);
+  zoom_dict d = zoom_dict_alloc(ctx, n_pairs, P, s, degr->blur_sigma, degr->feature, st);
   if (!d) return fail(ZOOM_ERR_OOM, "dictionary arrays");
   void* mem = d->lr_pix;
 
@@ -250,6 +252,7 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   sc.take<const float*>(n_images);
   sc.take<int32_t>(n_images);
   sc.take<int32_t>(n_images);
+  sc.take<int32_t>(n_images);
   sc.take<int32_t>(n_pairs * 3);
   Scratch scr(ctx, st);
   if (!scr.get(sc.off + 256)) {
@@ -261,16 +264,18 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   float* lr_all = s2.take<float>(lr_total);
   const float** d_lr_ptr = s2.take<const float*>(n_images);
   const float** d_hr_ptr = s2.take<const float*>(n_images);
+  int32_t* d_lr_h = s2.take<int32_t>(n_images);
   int32_t* d_lr_w = s2.take<int32_t>(n_images);
   int32_t* d_hr_w = s2.take<int32_t>(n_images);
   int32_t* d_pos = s2.take<int32_t>(n_pairs * 3);
   std::vector<const float*> h_lr_ptr(n_images), h_hr_ptr(n_images);
-  std::vector<int32_t> h_lr_w(n_images), h_hr_w(n_images);
+  std::vector<int32_t> h_lr_h(n_images), h_lr_w(n_images), h_hr_w(n_images);
   zoom_status rc = ZOOM_OK;
   for (int m = 0; m < n_images && rc == ZOOM_OK; ++m) {
     float* lr = lr_all + lr_off[m];
     h_lr_ptr[m] = lr;
     h_hr_ptr[m] = hr_images[m];
+    h_lr_h[m] = heights[m] / s;
     h_lr_w[m] = widths[m] / s;
     h_hr_w[m] = widths[m];
     cudaError_t e = launch_degrade_exact(hr_images[m], heights[m], widths[m], s, degr->blur_sigma,
@@ -284,13 +289,15 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_hr_ptr, h_hr_ptr.data(), n_images * sizeof(void*), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_lr_h, h_lr_h.data(), n_images * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_lr_w, h_lr_w.data(), n_images * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_hr_w, h_hr_w.data(), n_images * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_pos, positions, n_pairs * 12, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = launch_dict_gather(d_lr_ptr, d_lr_w, d_hr_ptr, d_hr_w, d_pos, n_pairs, P, s, d, st);
+      e = launch_dict_gather(d_lr_ptr, d_lr_h, d_lr_w, d_hr_ptr, d_hr_w, d_pos, n_pairs, P, s, d, st);
     // the host vectors must outlive the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = fail(ZOOM_ERR_CUDA, std::string("dictionary: ") + cudaGetErrorString(e));
@@ -311,12 +318,15 @@ void zoom_dict_destroy(zoom_dict d) {
   delete d;
 }
 
-zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma) {
+zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma,
+                           int32_t* feature, int32_t* feature_dim) {
   if (!d) return fail(ZOOM_ERR_INVALID_ARG, "NULL dictionary");
   if (n) *n = d->n;
   if (patch) *patch = d->P;
   if (scale) *scale = d->s;
   if (blur_sigma) *blur_sigma = d->blur_sigma;
+  if (feature) *feature = d->feature;
+  if (feature_dim) *feature_dim = d->d;
   return ZOOM_OK;
 }
 
@@ -337,7 +347,7 @@ zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_re
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(d->ctx->device));
   if (lr_pix)
-    ZCHECK_CUDA(cudaMemcpyAsync(lr_pix, d->lr_pix, d->n * d->d * 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK_CUDA(cudaMemcpyAsync(lr_pix, d->lr_pix, d->n * d->P * d->P * 4, cudaMemcpyDeviceToHost, st));
   if (mu) ZCHECK_CUDA(cudaMemcpyAsync(mu, d->mu, d->n * 4, cudaMemcpyDeviceToHost, st));
   if (hr_res)
     ZCHECK_CUDA(cudaMemcpy2DAsync(hr_res, d->ph2 * 4, d->hr_res, d->ph2pad * 4, d->ph2 * 4, d->n,
@@ -384,8 +394,8 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     c.take<int32_t>((N + 1) * L);
     c.take<int32_t>(N * L);
     c.take<int32_t>(L);
-    c.take<uint16_t>(ix->nd_rows * 80);
-    c.take<uint16_t>(ix->nd_rows * 32);
+    c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 0) * 8);
+    c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 1) * 8);
     ix->bytes = c.off + 256;
   }
   void* mem = zoom_alloc(ctx, ix->bytes, st);
@@ -401,8 +411,8 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->offs = c.take<int32_t>((N + 1) * L);
   ix->ids = c.take<int32_t>(N * L);
   ix->nuniq = c.take<int32_t>(L);
-  ix->dop16 = c.take<uint16_t>(ix->nd_rows * 80);
-  ix->dopbf = c.take<uint16_t>(ix->nd_rows * 32);
+  ix->dop16 = c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 0) * 8);
+  ix->dopbf = c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 1) * 8);
   zoom_status rc = ZOOM_OK;
   cudaError_t e = cudaMemcpyAsync(ix->alpha, alpha, (size_t)L * k * d->d * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ix->beta, beta, (size_t)L * k * 4, cudaMemcpyHostToDevice, st);
@@ -541,7 +551,7 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   }
   p.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
   p.q_rows = tc_rows_padded(nq, true);
-  p.KCH = p.prec == 0 ? 80 : 32;
+  p.KCH = tc_kc(d->d, p.prec) * 8;
   Carver c(nullptr);
   c.take<uint16_t>(p.q_rows * p.KCH);
   c.take<float>(nq);
@@ -582,7 +592,7 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
   zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
-    e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.MC,
+    e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.KCH / 8, pl.MC,
                       pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
@@ -613,7 +623,7 @@ zoom_status run_query_steps(zoom_index ix, const float* lr, int h, int w,
   zoom_ctx ctx = d->ctx;
   const int64_t nq = (int64_t)(h - d->P + 1) * (w - d->P + 1);
   zoom_stage_mark(ctx, 0, st);
-  cudaError_t e = launch_query_features(lr, h, w, d->P, d->dpad, b.feat, b.mu, b.norm2, st);
+  cudaError_t e = launch_query_features(lr, h, w, d->P, d->feature, d->dpad, b.feat, b.mu, b.norm2, st);
   zoom_stage_mark(ctx, 1, st);
   if (e == cudaSuccess)
     e = launch_hash(b.feat, d->dpad, d->d, nq, ix->alpha, ix->beta, ix->L, ix->k, ix->w, b.keys, st);
@@ -1093,7 +1103,7 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
       for (size_t k = 0; k < g.images.size(); ++k) {
         const int i = g.images[k];
         const int64_t o = g.q_off[k];
-        cudaError_t e = launch_query_features(lr[i], h[i], w[i], d->P, d->dpad, g.b.feat + o * d->dpad,
+        cudaError_t e = launch_query_features(lr[i], h[i], w[i], d->P, d->feature, d->dpad, g.b.feat + o * d->dpad,
                                               g.b.mu + o, nullptr, st);
         const int64_t nqi = (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1);
         if (e == cudaSuccess)
@@ -1153,7 +1163,7 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
         const int i = g.images[k];
         const int64_t o = g.q_off[k];
         const int64_t nqi = (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1);
-        e = launch_query_features(lr[i], h[i], w[i], d->P, d->dpad, g.b.feat + o * d->dpad, g.b.mu + o,
+        e = launch_query_features(lr[i], h[i], w[i], d->P, d->feature, d->dpad, g.b.feat + o * d->dpad, g.b.mu + o,
                                   nullptr, cs);
         if (e == cudaSuccess)
           e = launch_hash(g.b.feat + o * d->dpad, d->dpad, d->d, nqi, g.ix->alpha, g.ix->beta, g.ix->L,

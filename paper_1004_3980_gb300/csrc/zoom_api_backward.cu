@@ -191,7 +191,7 @@ zoom_status zoom_backward(zoom_index ix, const float* lr, int32_t h, int32_t w, 
   double* part = c.take<double>(2 * nblocks);
   char* rest = c.take<char>(0);
   // weights: given, or recomputed from the neighbours (Eq. 12-13)
-  ZB_CUDA(launch_query_features(lr, h, w, d->P, d->dpad, qfeat, mu, nullptr, st));
+  ZB_CUDA(launch_query_features(lr, h, w, d->P, d->feature, d->dpad, qfeat, mu, nullptr, st));
   const float* wv = wgt;
   if (!wv) {
     ZB_CUDA(launch_nbr_dist(qfeat, d->dpad, d->d, nq, d->feat, nbr, K, dist, st));

@@ -51,9 +51,10 @@ struct zoom_dict_s {
   zoom_ctx ctx = nullptr;
   int64_t n = 0;
   int P = 0, s = 0, d = 0, dpad = 0, PH = 0, ph2 = 0, ph2pad = 0;
+  int feature = 0;           // 0: pixels - mu (d = P^2); 1: first-order gradients (d = 2 P^2)
   double blur_sigma = 0.0;
-  float* lr_pix = nullptr;   // [N][d]
-  float* feat = nullptr;     // [N][dpad]  pixels - mu, zero padded
+  float* lr_pix = nullptr;   // [N][P^2]
+  float* feat = nullptr;     // [N][dpad]  feature, zero padded
   float* mu = nullptr;       // [N]
   float* norm2 = nullptr;    // [N]  ||feat||^2
   float* hr_res = nullptr;   // [N][ph2pad] HR patch - mu
@@ -73,8 +74,8 @@ struct zoom_index_s {
   int32_t* ids = nullptr;    // [L][N]   entry IDs grouped by bin, ascending within a bin
   int32_t* nuniq = nullptr;  // [L]
   // tensor-core operands of the dictionary: 128-row tiles [tile][kc][128][8]
-  uint16_t* dop16 = nullptr; // FP16 3-term split, 10 chunks of 8 per row
-  uint16_t* dopbf = nullptr; // BF16 single term, 4 chunks of 8 per row
+  uint16_t* dop16 = nullptr; // FP16 3-term split, tc_kc(d, 0) chunks of 8 per row
+  uint16_t* dopbf = nullptr; // BF16 single term, tc_kc(d, 1) chunks of 8 per row
   int64_t nd_rows = 0;       // rows of the operands (N rounded up to 128)
   size_t bytes = 0;
 };
@@ -86,7 +87,8 @@ struct zoom_index_s {
 void zoom_set_error(const std::string& msg);
 // A dictionary handle of n pairs with its (uninitialised) device arrays in
 // one allocation based at lr_pix; nullptr when the allocation fails.
-zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, cudaStream_t st);
+zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, int feature,
+                          cudaStream_t st);
 void* zoom_alloc(zoom_ctx ctx, size_t bytes, cudaStream_t st);
 void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st);
 
@@ -97,17 +99,18 @@ void zoom_free(zoom_ctx ctx, void* p, size_t bytes, cudaStream_t st);
 // dictionary / index build (kernels_build.cu)
 cudaError_t launch_degrade_exact(const float* hr, int H, int W, int s, double sigma, float* lr,
                                  cudaStream_t st);
-cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_w,
-                               const float* const* d_hr_images, const int32_t* d_hr_w,
-                               const int32_t* d_pos, int64_t n, int P, int s, zoom_dict d,
-                               cudaStream_t st);
+cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d_lr_h,
+                               const int32_t* d_lr_w, const float* const* d_hr_images,
+                               const int32_t* d_hr_w, const int32_t* d_pos, int64_t n, int P, int s,
+                               zoom_dict d, cudaStream_t st);
 cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const float* alpha,
                         const float* beta, int L, int k, float w, uint64_t* keys, cudaStream_t st);
 cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t csr_scratch_bytes(int64_t n);
 
 // per-query steps (kernels_query.cu)
-cudaError_t launch_query_features(const float* lr, int h, int w, int P, int dpad, float* feat,
+// F: feature mode (0 pixels minus mean, 1 first-order gradients)
+cudaError_t launch_query_features(const float* lr, int h, int w, int P, int F, int dpad, float* feat,
                                   float* mu, float* norm2, cudaStream_t st);
 cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t nq,
                                  int32_t* bucket_sum, unsigned long long* counters,
@@ -124,18 +127,31 @@ cudaError_t launch_knn_capped(zoom_index ix, const float* qfeat, const uint64_t*
 cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
                        const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
                        unsigned long long* counters, cudaStream_t st);
+// the same three steps for the gradient features, D = 18 or 50 (kernels_query_grad.cu)
+cudaError_t launch_knn_exact_grad(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
+                                  int K, int32_t* nbr, float* dist, unsigned long long* counters,
+                                  const int32_t* qidx, const unsigned long long* qcount, cudaStream_t st);
+cudaError_t launch_knn_capped_grad(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
+                                   int K, int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
+                                   unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_lle_grad(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
+                            const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
+                            unsigned long long* counters, cudaStream_t st);
 
 // tensor-core neighbour search (kernels_tc.cu)
 int64_t tc_rows_padded(int64_t n, bool even_tiles);
 cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
                            int precision, uint16_t* op, float* norm_out, cudaStream_t st);
-size_t tc_smem_bytes(int precision);
+// operand width in 8-element chunks for feature dimension d: FP16 split
+// (precision 0) 10 (K = 80, d <= 25) or 20 (K = 160, d = 50); BF16 4 or 8
+int tc_kc(int d, int precision);
+size_t tc_smem_bytes(int KC);
 int tc_list_size(int precision, int K, int rerank_mult);
 // tail_split > 0: whole query pairs round robin for the full rounds over the
 // grid, the remaining pairs cut into tail_split dictionary parts (nsplit must
 // equal tail_split); 0: nsplit round-robin splits of every pair
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
-                          int64_t nd, int precision, int MC, int nsplit, int tail_split, int grid,
+                          int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
                           float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st);
 // ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
 // chunk index), ascending; exact = 1 for the FP16-split filter (proof and

@@ -30,7 +30,7 @@ constexpr size_t kStage = 64u << 20;   // host staging buffer of the copies
 
 struct DictHeader {
   char magic[8];
-  uint32_t version, reserved;
+  uint32_t version, feature;   // feature mode (0 pixels - mean, 1 gradients)
   int64_t n;
   int32_t P, s, d, dpad, ph2, ph2pad;
   double blur_sigma;
@@ -102,6 +102,7 @@ zoom_status zoom_dict_save(zoom_dict d, const char* path, void* stream) {
   DictHeader h{};
   memcpy(h.magic, kDictMagic, 8);
   h.version = kVersion;
+  h.feature = (uint32_t)d->feature;
   h.n = d->n;
   h.P = d->P;
   h.s = d->s;
@@ -114,7 +115,7 @@ zoom_status zoom_dict_save(zoom_dict d, const char* path, void* stream) {
   std::vector<char> stage(kStage);
   std::string why;
   const int64_t n = d->n;
-  if (!write_dev(fl.f, d->lr_pix, (size_t)n * d->d * 4, stage, st, why) ||
+  if (!write_dev(fl.f, d->lr_pix, (size_t)n * d->P * d->P * 4, stage, st, why) ||
       !write_dev(fl.f, d->feat, (size_t)n * d->dpad * 4, stage, st, why) ||
       !write_dev(fl.f, d->mu, (size_t)n * 4, stage, st, why) ||
       !write_dev(fl.f, d->norm2, (size_t)n * 4, stage, st, why) ||
@@ -133,17 +134,18 @@ zoom_status zoom_dict_load(zoom_ctx ctx, const char* path, void* stream, zoom_di
   if (fread(&h, sizeof(h), 1, fl.f) != 1) return fail(ZOOM_ERR_IO, "file truncated");
   if (memcmp(h.magic, kDictMagic, 8) != 0) return fail(ZOOM_ERR_INVALID_ARG, "not a dictionary file");
   if (h.version != kVersion) return fail(ZOOM_ERR_INVALID_ARG, "unsupported dictionary file version");
-  if ((h.P != 3 && h.P != 5) || h.s < 1 || h.s > 4 || h.n < 1 || h.n > (1LL << 30) || h.d != h.P * h.P ||
+  if ((h.P != 3 && h.P != 5) || h.s < 1 || h.s > 4 || h.n < 1 || h.n > (1LL << 30) || h.feature > 1 ||
+      h.d != (h.feature ? 2 : 1) * h.P * h.P ||
       h.dpad != (h.d + 3) / 4 * 4 || h.ph2 != h.s * h.P * h.s * h.P || h.ph2pad != (h.ph2 + 3) / 4 * 4 ||
       !(h.blur_sigma > 0.0))
     return fail(ZOOM_ERR_INVALID_ARG, "dictionary file header out of range");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ZOOM_ERR_CUDA, "cudaSetDevice");
-  zoom_dict d = zoom_dict_alloc(ctx, h.n, h.P, h.s, h.blur_sigma, st);
+  zoom_dict d = zoom_dict_alloc(ctx, h.n, h.P, h.s, h.blur_sigma, (int)h.feature, st);
   if (!d) return fail(ZOOM_ERR_OOM, "dictionary arrays");
   std::vector<char> stage(kStage);
   std::string why;
   const int64_t n = d->n;
-  const bool ok = read_dev(fl.f, d->lr_pix, (size_t)n * d->d * 4, stage, st, why) &&
+  const bool ok = read_dev(fl.f, d->lr_pix, (size_t)n * d->P * d->P * 4, stage, st, why) &&
                   read_dev(fl.f, d->feat, (size_t)n * d->dpad * 4, stage, st, why) &&
                   read_dev(fl.f, d->mu, (size_t)n * 4, stage, st, why) &&
                   read_dev(fl.f, d->norm2, (size_t)n * 4, stage, st, why) &&

@@ -130,7 +130,9 @@ class Dictionary:
     """LR/HR patch-pair dictionary built on the device (zoom_build_dictionary)."""
 
     def __init__(self, ctx: Context, hr_images, positions, scale: int, patch: int,
-                 blur_sigma: float = 0.8, stream=None):
+                 blur_sigma: float = 0.8, stream=None, feature: int = 0):
+        """feature: 0 = LR pixels minus their mean, 1 = first-order gradients
+        of the LR image at the patch's pixels (Sec. 4.1)."""
         self.ctx = ctx
         for t in hr_images:
             _need(t, torch.float32, "hr image")
@@ -139,7 +141,7 @@ class Dictionary:
         ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hr_images])
         hs = (C.c_int32 * n)(*[t.shape[0] for t in hr_images])
         ws = (C.c_int32 * n)(*[t.shape[1] for t in hr_images])
-        degr = capi.Degradation(scale, patch, blur_sigma)
+        degr = capi.Degradation(scale, patch, blur_sigma, feature)
         h = C.c_void_p()
         capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), len(pos),
                   pos.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream), C.byref(h))
@@ -149,8 +151,11 @@ class Dictionary:
         self.handle = h
         _LIVE["dict"].add(self)
         n, P, s, sig = C.c_int64(), C.c_int32(), C.c_int32(), C.c_double()
-        capi.call("zoom_dict_info", h, C.byref(n), C.byref(P), C.byref(s), C.byref(sig))
+        f, dim = C.c_int32(), C.c_int32()
+        capi.call("zoom_dict_info", h, C.byref(n), C.byref(P), C.byref(s), C.byref(sig), C.byref(f),
+                  C.byref(dim))
         self.n, self.patch, self.scale, self.blur_sigma = n.value, P.value, s.value, sig.value
+        self.feature, self.dim = f.value, dim.value
 
     def save(self, path: str, stream=None) -> None:
         """Writes every stored array to a file (zoom_dict_save)."""
@@ -199,6 +204,8 @@ class Index:
         self.dictionary = dictionary
         a = np.ascontiguousarray(alpha, np.float32)
         b = np.ascontiguousarray(beta, np.float32)
+        if a.shape != (L * k, dictionary.dim) or b.shape != (L * k,):
+            raise ValueError(f"alpha must be [{L * k}][{dictionary.dim}] and beta [{L * k}]")
         prm = capi.LshParams(L, k, w, min_table_hits, max_candidates)
         h = C.c_void_p()
         capi.call("zoom_build_index", dictionary.handle, C.byref(prm), a.ctypes.data, b.ctypes.data,
@@ -228,8 +235,8 @@ class Index:
         return self
 
     def params(self, stream=None):
-        """The random draws (alpha [L*k][P*P], beta [L*k]) as numpy float32 (zoom_export_params)."""
-        d = self.dictionary.patch ** 2
+        """The random draws (alpha [L*k][D], beta [L*k]) as numpy float32 (zoom_export_params)."""
+        d = self.dictionary.dim
         alpha = np.empty((self.L * self.k, d), np.float32)
         beta = np.empty(self.L * self.k, np.float32)
         capi.call("zoom_export_params", self.handle, alpha.ctypes.data, beta.ctypes.data, _stream(stream))
