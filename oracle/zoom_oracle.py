@@ -115,10 +115,32 @@ def gradient_images(img: np.ndarray):
     return x[:, cp] - x[:, cm], x[rp, :] - x[rm, :]
 
 
+def second_order_images(img: np.ndarray):
+    """Second-order gradients of an image (Sec. 4.1, "Feature representation":
+    convolution with [-1, 0, 2, 0, -1] and its transpose):
+    g_xx(r, c) = 2 x(r, c) - x(r, c-2) - x(r, c+2), and g_yy likewise along
+    the rows.  Readings: borders clamp to the edge, as for the first order."""
+    x = np.asarray(img, dtype=np.float64)
+    h, w = x.shape
+    cm, cp = np.maximum(np.arange(w) - 2, 0), np.minimum(np.arange(w) + 2, w - 1)
+    rm, rp = np.maximum(np.arange(h) - 2, 0), np.minimum(np.arange(h) + 2, h - 1)
+    return 2.0 * x - x[:, cm] - x[:, cp], 2.0 * x - x[rm, :] - x[rp, :]
+
+
 # Feature modes of a dictionary (Sec. 4.1): 0 = the LR patch minus its mean
 # (P*P values); 1 = the first-order gradients of the LR image at the patch's
-# pixels (g_x row-major, then g_y: 2*P*P values).
-FEATURE_DIMS = {0: lambda P: P * P, 1: lambda P: 2 * P * P}
+# pixels (g_x row-major, then g_y: 2*P*P values); 2 = the second-order
+# gradients, laid out the same way (g_xx, then g_yy).
+FEATURE_DIMS = {0: lambda P: P * P, 1: lambda P: 2 * P * P, 2: lambda P: 2 * P * P}
+
+
+def gradient_fn(feature: int):
+    """The gradient filter pair of a gradient feature mode (1 or 2)."""
+    if feature == 1:
+        return gradient_images
+    if feature == 2:
+        return second_order_images
+    raise ValueError("feature must be 0, 1 or 2")
 
 
 def patch_features(img: np.ndarray, P: int, feature: int = 0):
@@ -126,7 +148,8 @@ def patch_features(img: np.ndarray, P: int, feature: int = 0):
 
     Sec. 4.1 ("Feature representation") hashes a feature of the LR patch:
     feature 0 is the mean-subtracted patch, feature 1 the first-order
-    gradients of the image at the patch's pixels (``gradient_images``)."""
+    gradients of the image at the patch's pixels (``gradient_images``),
+    feature 2 the second-order ones (``second_order_images``)."""
     x = np.asarray(img, dtype=np.float64)
     ii, jj = patch_origins(x.shape[0], x.shape[1], P)
     n = len(ii)
@@ -137,9 +160,7 @@ def patch_features(img: np.ndarray, P: int, feature: int = 0):
     mu = px.mean(axis=1)
     if feature == 0:
         return px - mu[:, None], mu
-    if feature != 1:
-        raise ValueError("feature must be 0 or 1")
-    gx, gy = gradient_images(x)
+    gx, gy = gradient_fn(feature)(x)
     v = np.empty((n, 2 * P * P))
     for a in range(P):
         for b in range(P):
@@ -183,8 +204,8 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature
     Readings: the LR training image is stored at float32, the precision of the
     test LR image; the LR patch mean is subtracted from both patches and is
     added back at reconstruction time.  Position k in ``positions`` (sorted by
-    image, row, column) is the unique ID k.  Feature 1: the gradients of the
-    whole (float32) LR training image at the patch's pixels."""
+    image, row, column) is the unique ID k.  Features 1 and 2: the gradients
+    of the whole (float32) LR training image at the patch's pixels."""
     lr_imgs = [degrade(np.asarray(x, np.float64), s, sigma).astype(np.float32) for x in hr_images]
     PH = s * P
     N = len(positions)
@@ -198,7 +219,7 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature
     if feature == 0:
         feat = lr64 - mu[:, None]
     else:
-        grads = [gradient_images(x) for x in lr_imgs]
+        grads = [gradient_fn(feature)(x) for x in lr_imgs]
         feat = np.empty((N, 2 * P * P))
         for n, (m, i, j) in enumerate(np.asarray(positions)):
             gx, gy = grads[m]

@@ -134,3 +134,16 @@ def test_swapped_gradient_halves_are_caught(monkeypatch):
     orig = O.gradient_images
     monkeypatch.setattr(O, "gradient_images", lambda img: orig(img)[::-1])
     _fails(TF.test_gradient_feature_layout_brute_force, np.random.default_rng(0), 5)
+
+
+def test_second_order_with_unit_spacing_is_caught(monkeypatch):
+    # [-1, 2, -1] (adjacent pixels) in place of [-1, 0, 2, 0, -1]
+    def lap1(img):
+        x = np.asarray(img, np.float64)
+        h, w = x.shape
+        cm, cp = np.maximum(np.arange(w) - 1, 0), np.minimum(np.arange(w) + 1, w - 1)
+        rm, rp = np.maximum(np.arange(h) - 1, 0), np.minimum(np.arange(h) + 1, h - 1)
+        return 2 * x - x[:, cm] - x[:, cp], 2 * x - x[rm, :] - x[rp, :]
+    monkeypatch.setattr(O, "second_order_images", lap1)
+    _fails(TF.test_second_order_of_a_quadratic_and_a_ramp)
+    _fails(TF.test_second_order_feature_layout_brute_force, np.random.default_rng(0))
