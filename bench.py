@@ -44,6 +44,7 @@ import synth_inputs as S  # noqa: E402
 
 METRIC = "HR megapixels/s"
 UNIT = "MP/s"
+GRAD_W = 8.0   # bin width of the gradient-feature extra
 
 
 def parse():
@@ -395,6 +396,37 @@ def run_single(a, wl, config, rank, world, local):
                             "max_candidates": cap, "distances_per_query": cap,
                             "psnr_vs_uncapped_db": 10 * np.log10(1.0 / max(mse3, 1e-30))}
         ixc.close()
+        # gradient features (Sec. 4.1): the same workload with the 2 P^2 = 50
+        # first-order gradients of each LR patch as its feature; w = 8 puts
+        # about the pixel form's share of the dictionary in the candidate set.
+        # Exact form: the FP16-split filter at K = 160.
+        d_g = Z.Dictionary(ctx, [torch.from_numpy(x).cuda() for x in train], pos, wl.scale, wl.patch,
+                           wl.blur_sigma, feature=1)
+        D_g = 2 * wl.patch ** 2
+        a_g, b_g = S.lsh_draws(wl.proj_seed, wl.L, wl.k, D_g, GRAD_W)
+        ixg = Z.Index(d_g, wl.L, wl.k, GRAD_W, a_g, b_g)
+        for _ in range(2):
+            Z.upscale(ixg, lr, prm, out=out)
+        ms4 = timed_steps(lambda: Z.upscale(ixg, lr, prm, out=out), a.steps, st, torch, world)
+        ctx.set_stage_timing(True)
+        filt_g = []
+        for _ in range(3):
+            Z.upscale(ixg, lr, prm, out=out)
+            filt_g.append(ctx.stats()["ms_stage"].get("knn_filter_kernel", 0.0))
+        ctx.set_stage_timing(False)
+        st_g = ctx.stats()
+        fg = float(np.mean(filt_g))
+        ach_g = nq * wl.n_pairs * 2.0 * 160 / (fg / 1e3) / 1e12 if fg > 0 else None
+        res["gradient_features"] = {
+            "value": world * hr_px / 1e6 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4,
+            "feature_dim": D_g, "w": GRAD_W, "mean_bucket_sum_per_query": st_g["mean_bucket_sum"],
+            "filter_fallback_queries": st_g["n_filter_fallback"],
+            "roofline": {"kernel": "k_knn_tc<20,16,0> (FP16 split, K = 160)", "bound": "tensor",
+                         "achieved": ach_g, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": ach_g / tc_peak if ach_g else None, "kernel_ms": fg,
+                         "work": f"{nq} queries x {wl.n_pairs} entries x 2 x 160 flops"}}
+        ixg.close()
+        d_g.close()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_oracle_sample(wl, train, pos, alpha, beta, lr_np, a.cpu_sample_queries)
     return res

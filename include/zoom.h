@@ -68,8 +68,10 @@ typedef struct {
  * 1 = the first-order gradients of the LR image at the patch's pixels,
  * g_x(r,c) = x(r,c+1) - x(r,c-1) then g_y(r,c) = x(r+1,c) - x(r-1,c), each
  * row-major over the patch, image coordinates clamped to the image (2*P*P
- * values).  Either way the HR patch is stored and blended relative to the LR
- * patch mean.  Supported: scale 1..4, blur_sigma > 0, feature 0 or 1;
+ * values); 2 = the second-order gradients in the same layout, g_xx(r,c) =
+ * 2x(r,c) - x(r,c-2) - x(r,c+2) then g_yy.  Either way the HR patch is
+ * stored and blended relative to the LR patch mean.  Supported: scale 1..4,
+ * blur_sigma > 0, feature 0, 1 or 2;
  * dictionaries and queries need lr_patch 3 or 5 (UNSUPPORTED otherwise); the
  * image-only calls (zoom_backproject, zoom_degrade, their adjoints) ignore
  * lr_patch and feature. */

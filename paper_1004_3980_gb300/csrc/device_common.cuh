@@ -41,29 +41,39 @@ __device__ __forceinline__ int zoom_clampi(int v, int lo, int hi) {
 }
 
 // Feature dimension of a P x P patch: the pixels minus their mean (mode 0) or
-// the first-order gradients at the patch's pixels (mode 1).
+// the first- or second-order gradients at the patch's pixels (modes 1, 2).
 __host__ __device__ constexpr int zoom_feature_dim(int P, int F) { return F ? 2 * P * P : P * P; }
 
-// First-order gradient feature of the P x P patch at (i, j) of an h x w image
-// (row stride ld): g_x(r, c) = x(r, c+1) - x(r, c-1), g_y(r, c) = x(r+1, c) -
-// x(r-1, c) (the correlation with [-1, 0, 1] and its transpose), coordinates
-// clamped to the image; v = [g_x | g_y], each row-major over the patch, and
-// norm2 = sum of v^2 (sequential FMA).  Dictionary entries and queries share
-// it, so equal neighbourhoods give bit-identical features.
-template <int P>
+// Gradient feature of the P x P patch at (i, j) of an h x w image (row
+// stride ld), image coordinates clamped to the image.  ORDER 1: g_x(r, c) =
+// x(r, c+1) - x(r, c-1), g_y(r, c) = x(r+1, c) - x(r-1, c) (the correlation
+// with [-1, 0, 1] and its transpose).  ORDER 2: g_xx(r, c) = 2 x(r, c) -
+// x(r, c-2) - x(r, c+2) and g_yy likewise ([-1, 0, 2, 0, -1]).  v = [g_x |
+// g_y], each row-major over the patch; norm2 = sum of v^2 (sequential FMA).
+// Dictionary entries and queries share it, so equal neighbourhoods give
+// bit-identical features.
+template <int P, int ORDER>
 __device__ __forceinline__ void zoom_gradient_feature(const float* __restrict__ img, int h, int w,
                                                       size_t ld, int i, int j, float (&v)[2 * P * P],
                                                       float& norm2) {
 #pragma unroll
   for (int a = 0; a < P; ++a) {
     const int r = i + a;
-    const int rm = r > 0 ? r - 1 : 0, rp = r + 1 < h ? r + 1 : h - 1;
+    const int rm = r - ORDER > 0 ? r - ORDER : 0, rp = r + ORDER < h ? r + ORDER : h - 1;
 #pragma unroll
     for (int b = 0; b < P; ++b) {
       const int c = j + b;
-      const int cm = c > 0 ? c - 1 : 0, cp = c + 1 < w ? c + 1 : w - 1;
-      v[a * P + b] = img[(size_t)r * ld + cp] - img[(size_t)r * ld + cm];
-      v[P * P + a * P + b] = img[(size_t)rp * ld + c] - img[(size_t)rm * ld + c];
+      const int cm = c - ORDER > 0 ? c - ORDER : 0, cp = c + ORDER < w ? c + ORDER : w - 1;
+      const float xm = img[(size_t)r * ld + cm], xp = img[(size_t)r * ld + cp];
+      const float ym = img[(size_t)rm * ld + c], yp = img[(size_t)rp * ld + c];
+      if constexpr (ORDER == 1) {
+        v[a * P + b] = xp - xm;
+        v[P * P + a * P + b] = yp - ym;
+      } else {
+        const float x0 = img[(size_t)r * ld + c];
+        v[a * P + b] = fmaf(2.f, x0, -xm) - xp;
+        v[P * P + a * P + b] = fmaf(2.f, x0, -ym) - yp;
+      }
     }
   }
   float n2 = 0.f;

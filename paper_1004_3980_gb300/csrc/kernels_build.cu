@@ -84,7 +84,7 @@ __global__ void k_dict_gather(const float* const* __restrict__ lr_images,
     for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? v[q] : 0.f;
   } else {
     float g[D];
-    zoom_gradient_feature<P>(lr, lr_h[m], lw, (size_t)lw, i, j, g, n2);
+    zoom_gradient_feature<P, F>(lr, lr_h[m], lw, (size_t)lw, i, j, g, n2);
     for (int q = 0; q < dpad; ++q) feat[e * dpad + q] = q < D ? g[q] : 0.f;
   }
   mu[e] = mean;
@@ -354,6 +354,8 @@ cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d
   else if (P == 5 && d->feature == 0) ZOOM_GATHER(5, 0);
   else if (P == 3 && d->feature == 1) ZOOM_GATHER(3, 1);
   else if (P == 5 && d->feature == 1) ZOOM_GATHER(5, 1);
+  else if (P == 3 && d->feature == 2) ZOOM_GATHER(3, 2);
+  else if (P == 5 && d->feature == 2) ZOOM_GATHER(5, 2);
   else return cudaErrorInvalidValue;
 #undef ZOOM_GATHER
   return cudaGetLastError();

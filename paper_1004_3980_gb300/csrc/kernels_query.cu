@@ -11,7 +11,8 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // query features: every P x P patch of the LR image at stride 1, row order;
-// F = 0 pixels minus their mean, F = 1 first-order gradients (Sec. 4.1)
+// F = 0 pixels minus their mean, F = 1, 2 first- or second-order gradients
+// (Sec. 4.1)
 // ---------------------------------------------------------------------------
 template <int P, int F>
 __global__ void k_query_features(const float* __restrict__ lr, int h, int w, int dpad,
@@ -34,7 +35,7 @@ __global__ void k_query_features(const float* __restrict__ lr, int h, int w, int
     for (int t = 0; t < dpad; ++t) feat[q * dpad + t] = t < D ? v[t] : 0.f;
   } else {
     float g[D];
-    zoom_gradient_feature<P>(lr, h, w, (size_t)w, i, j, g, n2);
+    zoom_gradient_feature<P, F>(lr, h, w, (size_t)w, i, j, g, n2);
     for (int t = 0; t < dpad; ++t) feat[q * dpad + t] = t < D ? g[t] : 0.f;
   }
   mu[q] = m;
@@ -97,6 +98,10 @@ cudaError_t launch_query_features(const float* lr, int h, int w, int P, int F, i
     k_query_features<3, 1><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
   else if (P == 5 && F == 1)
     k_query_features<5, 1><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
+  else if (P == 3 && F == 2)
+    k_query_features<3, 2><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
+  else if (P == 5 && F == 2)
+    k_query_features<5, 2><<<blocks, 128, 0, st>>>(lr, h, w, dpad, feat, mu, norm2);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -45,21 +45,24 @@ __host__ __device__ constexpr int tc_threads(int MC) { return (9 + tc_mma_warps(
 constexpr int kBarBytes = 512;
 constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
 // Per epilogue lane, chunks below the threshold are first appended to a
-// shared-memory buffer of kBuf slots (a few instructions each) and merged
+// shared-memory buffer of tc_buf(KC) slots (a few instructions each) and merged
 // into the sorted register list when some lane of the warp runs out of room:
 // the merge loop then runs for all lanes together, so the sorted insertions
-// execute with the warp converged.
-constexpr int kBuf = 16;
+// execute with the warp converged.  A tile adds at most 4 entries per lane,
+// so 8 slots suffice; 16 flush half as often.  The widest operands (K = 160)
+// take 8, which frees room for a third ring stage.
+__host__ __device__ constexpr int tc_buf(int KC) { return KC >= 20 ? 8 : 16; }
 constexpr int kSmemMax = 232448;  // shared memory a CTA may opt into (227 KB)
 // Dictionary-tile ring depth: as many bulk copies in flight as the shared
 // memory left by the two query tiles, the barriers and the append buffers
-// holds, up to 16 (KC = 4: 16, 8: 10, 10: 7, 20: 2).
+// holds, up to 16 (KC = 4: 16, 8: 10, 10: 7, 20: 3).
 __host__ __device__ constexpr int tc_stages(int KC) {
-  return (kSmemMax - 1024 - kBarBytes - kBuf * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16) < 16
-             ? (kSmemMax - 1024 - kBarBytes - kBuf * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16)
+  return (kSmemMax - 1024 - kBarBytes - tc_buf(KC) * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16) < 16
+             ? (kSmemMax - 1024 - kBarBytes - tc_buf(KC) * 256 * 8 - 2 * KC * TC_ROWS * 16) /
+                   (KC * TC_ROWS * 16)
              : 16;
 }
-static_assert(tc_stages(4) == 16 && tc_stages(8) == 10 && tc_stages(10) == 7 && tc_stages(20) == 2,
+static_assert(tc_stages(4) == 16 && tc_stages(8) == 10 && tc_stages(10) == 7 && tc_stages(20) == 3,
               "ring depths");
 constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
 
@@ -365,6 +368,7 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
   uint64_t* acc_empty = acc_full + 4;          // [2][2]
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  constexpr int kBuf = tc_buf(KC);
   float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBuf][256]
   int* buf_i = (int*)(buf_v + kBuf * 256);               // [kBuf][256]
 
@@ -1014,7 +1018,7 @@ cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_
 
 size_t tc_smem_bytes(int KC) {
   // alignment pad + operand tiles + barriers + the epilogue append buffers
-  return 1024 + (size_t)(2 + tc_stages(KC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)kBuf * 256 * 8;
+  return 1024 + (size_t)(2 + tc_stages(KC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)tc_buf(KC) * 256 * 8;
 }
 
 int tc_list_size(int precision, int K, int rerank_mult) {

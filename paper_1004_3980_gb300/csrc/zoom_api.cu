@@ -218,7 +218,7 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
   if (s < 1 || s > 4) return fail(ZOOM_ERR_INVALID_ARG, "scale must be in 1..4");
   if (P != 3 && P != 5) return fail(ZOOM_ERR_UNSUPPORTED, "lr_patch must be 3 or 5");
   if (!(degr->blur_sigma > 0.f)) return fail(ZOOM_ERR_INVALID_ARG, "blur_sigma must be > 0");
-  if (degr->feature != 0 && degr->feature != 1) return fail(ZOOM_ERR_INVALID_ARG, "feature must be 0 or 1");
+  if (degr->feature < 0 || degr->feature > 2) return fail(ZOOM_ERR_INVALID_ARG, "feature must be 0, 1 or 2");
   if (n_images < 1 || n_pairs < 1 || n_pairs > (1LL << 30))
     return fail(ZOOM_ERR_INVALID_ARG, "n_images and n_pairs must be positive");
   for (int m = 0; m < n_images; ++m) {

@@ -51,7 +51,7 @@ struct zoom_dict_s {
   zoom_ctx ctx = nullptr;
   int64_t n = 0;
   int P = 0, s = 0, d = 0, dpad = 0, PH = 0, ph2 = 0, ph2pad = 0;
-  int feature = 0;           // 0: pixels - mu (d = P^2); 1: first-order gradients (d = 2 P^2)
+  int feature = 0;           // 0: pixels - mu (d = P^2); 1 / 2: first / second-order gradients (d = 2 P^2)
   double blur_sigma = 0.0;
   float* lr_pix = nullptr;   // [N][P^2]
   float* feat = nullptr;     // [N][dpad]  feature, zero padded
@@ -109,7 +109,7 @@ cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes,
 size_t csr_scratch_bytes(int64_t n);
 
 // per-query steps (kernels_query.cu)
-// F: feature mode (0 pixels minus mean, 1 first-order gradients)
+// F: feature mode (0 pixels minus mean, 1 / 2 first / second-order gradients)
 cudaError_t launch_query_features(const float* lr, int h, int w, int P, int F, int dpad, float* feat,
                                   float* mu, float* norm2, cudaStream_t st);
 cudaError_t launch_bucket_lookup(zoom_index ix, const uint64_t* qkeys, int64_t nq,

@@ -30,7 +30,7 @@ constexpr size_t kStage = 64u << 20;   // host staging buffer of the copies
 
 struct DictHeader {
   char magic[8];
-  uint32_t version, feature;   // feature mode (0 pixels - mean, 1 gradients)
+  uint32_t version, feature;   // feature mode (0 pixels - mean, 1 / 2 gradients)
   int64_t n;
   int32_t P, s, d, dpad, ph2, ph2pad;
   double blur_sigma;
@@ -134,7 +134,7 @@ zoom_status zoom_dict_load(zoom_ctx ctx, const char* path, void* stream, zoom_di
   if (fread(&h, sizeof(h), 1, fl.f) != 1) return fail(ZOOM_ERR_IO, "file truncated");
   if (memcmp(h.magic, kDictMagic, 8) != 0) return fail(ZOOM_ERR_INVALID_ARG, "not a dictionary file");
   if (h.version != kVersion) return fail(ZOOM_ERR_INVALID_ARG, "unsupported dictionary file version");
-  if ((h.P != 3 && h.P != 5) || h.s < 1 || h.s > 4 || h.n < 1 || h.n > (1LL << 30) || h.feature > 1 ||
+  if ((h.P != 3 && h.P != 5) || h.s < 1 || h.s > 4 || h.n < 1 || h.n > (1LL << 30) || h.feature > 2 ||
       h.d != (h.feature ? 2 : 1) * h.P * h.P ||
       h.dpad != (h.d + 3) / 4 * 4 || h.ph2 != h.s * h.P * h.s * h.P || h.ph2pad != (h.ph2 + 3) / 4 * 4 ||
       !(h.blur_sigma > 0.0))

@@ -1,11 +1,11 @@
-"""Gradient features (Sec. 4.1, feature mode 1: first-order gradients of the
-LR image at the patch's pixels, D = 2 P^2) through every search path of the
-C ABI, against the oracle with the same seeded inputs: the features via the
-bucket keys and the neighbour distances, the SIMT scan, the exact
-tensor-core filter (bit-identical to the scan; K = 80 operands for P = 3,
-K = 160 for P = 5), the BF16 filter (recall), the capped walk and the whole
-upscale.  Bin widths give candidate sets of about a fifth of the dictionary,
-so LSH membership matters."""
+"""Gradient features (Sec. 4.1, feature modes 1 and 2: the first- and
+second-order gradients of the LR image at the patch's pixels, D = 2 P^2)
+through every search path of the C ABI, against the oracle with the same
+seeded inputs: the features via the bucket keys and the neighbour
+distances, the SIMT scan, the exact tensor-core filter (bit-identical to the
+scan; K = 80 operands for P = 3, K = 160 for P = 5), the BF16 filter
+(recall), the capped walk and the whole upscale.  Bin widths give candidate
+sets of a seventh to a third of the dictionary, so LSH membership matters."""
 import dataclasses
 
 import numpy as np
@@ -20,12 +20,13 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module", params=[(3, 1.5), (5, 3.0)], ids=["P3_D18", "P5_D50"])
+@pytest.fixture(scope="module", params=[(3, 1.5, 1), (5, 3.0, 1), (3, 2.0, 2), (5, 4.0, 2)],
+                ids=["first_P3_D18", "first_P5_D50", "second_P3_D18", "second_P5_D50"])
 def grad(request):
     from paper_1004_3980_gb300 import build
     build.build()
     import paper_1004_3980_gb300 as Z
-    P, w = request.param
+    P, w, F = request.param
     wl = dataclasses.replace(S.WORKLOADS["zoom2x_64_dict20k"], patch=P, n_pairs=8000, lr_h=32, lr_w=36, w=w)
     train = S.training_images(wl, 8)
     lrs = wl.train_hr // wl.scale
@@ -33,15 +34,15 @@ def grad(request):
     D = 2 * P * P
     alpha, beta = S.lsh_draws(wl.proj_seed, wl.L, wl.k, D, w)
     lr = S.test_image(wl)
-    odict = O.build_dictionary(train, pos, wl.scale, P, wl.blur_sigma, feature=1)
+    odict = O.build_dictionary(train, pos, wl.scale, P, wl.blur_sigma, feature=F)
     oindex = O.build_index(odict, alpha, beta, w, wl.L, wl.k)
     oq = O.query(lr, odict, oindex, wl.K + 1, wl.reg_rel)
     ctx = Z.Context(0)
     d = Z.Dictionary(ctx, [torch.from_numpy(x).cuda() for x in train], pos, wl.scale, P, wl.blur_sigma,
-                     feature=1)
+                     feature=F)
     ix = Z.Index(d, wl.L, wl.k, w, alpha, beta)
     return dict(wl=wl, train=train, pos=pos, alpha=alpha, beta=beta, lr=lr, odict=odict, oindex=oindex,
-                oq=oq, ctx=ctx, d=d, ix=ix, D=D)
+                oq=oq, ctx=ctx, d=d, ix=ix, D=D, F=F)
 
 
 def _q(g, **kw):
@@ -52,7 +53,7 @@ def _q(g, **kw):
 
 def test_dictionary_and_keys(grad):
     g = grad
-    assert g["d"].feature == 1 and g["d"].dim == g["D"]
+    assert g["d"].feature == g["F"] and g["d"].dim == g["D"]
     keys, _ = g["ix"].export_keys()
     ok = g["oindex"].margin >= 1e-5
     assert ok.mean() > 0.95
@@ -166,7 +167,7 @@ def test_save_and_load_keep_the_feature_mode(grad, tmp_path):
     p = str(tmp_path / "grad.zd")
     g["d"].save(p)
     d2 = Z.Dictionary.load(g["ctx"], p)
-    assert d2.feature == 1 and d2.dim == g["D"]
+    assert d2.feature == g["F"] and d2.dim == g["D"]
     wl = g["wl"]
     ix2 = Z.Index(d2, wl.L, wl.k, wl.w, g["alpha"], g["beta"])
     assert np.array_equal(ix2.export_keys()[0], g["ix"].export_keys()[0])
