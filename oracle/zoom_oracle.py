@@ -243,6 +243,51 @@ def dictionary_from_lr_hr(lr_img, hr_img, s: int, P: int, feature: int = 0) -> D
 
 
 # ---------------------------------------------------------------------------
+# Training-crop sampling (Sec. 5.1 "Training Data Generation")
+# ---------------------------------------------------------------------------
+
+
+def gradient_magnitude(img: np.ndarray) -> np.ndarray:
+    """Sec. 5.1: the horizontal and vertical first-order gradients at every
+    pixel (``gradient_images``), combined per pixel.  Reading: the Euclidean
+    magnitude sqrt(g_x^2 + g_y^2), in FP64."""
+    gx, gy = gradient_images(img)
+    return np.sqrt(gx * gx + gy * gy)
+
+
+def sample_crop_centers(img: np.ndarray, u: np.ndarray):
+    """Sec. 5.1: a CDF over the pixels from their gradient values, and the
+    centre pixel of a crop drawn from it, for each uniform draw u in [0, 1)
+    (the draws are inputs).  Readings: pixels in row-major order, mass =
+    gradient magnitude; the drawn pixel is the first whose cumulative mass
+    exceeds u * total (so a pixel without mass is never drawn); a flat image
+    (no mass) draws uniformly, pixel floor(u * n).  Returns int64 rows and
+    columns."""
+    x = np.asarray(img, dtype=np.float64)
+    h, w = x.shape
+    n = h * w
+    u = np.asarray(u, dtype=np.float64)
+    cdf = np.cumsum(gradient_magnitude(x).ravel())
+    total = cdf[-1]
+    if total > 0:
+        idx = np.searchsorted(cdf, u * total, side="right")
+    else:
+        idx = np.floor(u * n).astype(np.int64)
+    idx = np.minimum(idx, n - 1)
+    return idx // w, idx % w
+
+
+def crop_windows(rows, cols, h: int, w: int, ch: int, cw: int):
+    """Top-left corners of ch x cw crops centred at (rows, cols) (Sec. 5.1:
+    a crop centred at the drawn pixel).  Reading: the centre of an even side
+    is the pixel after the middle (top = row - ch // 2), and a window that
+    would leave the image is shifted inside it."""
+    top = np.clip(np.asarray(rows) - ch // 2, 0, h - ch)
+    left = np.clip(np.asarray(cols) - cw // 2, 0, w - cw)
+    return top, left
+
+
+# ---------------------------------------------------------------------------
 # Hashing (Sec. 3.2; Sec. 4.1, Eq. 10)
 # ---------------------------------------------------------------------------
 

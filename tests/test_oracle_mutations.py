@@ -12,6 +12,7 @@ from tests import test_oracle_features as TF
 from tests import test_oracle_hash as TH
 from tests import test_oracle_knn_lle as TK
 from tests import test_oracle_recon_bp as TR
+from tests import test_oracle_sampling as TS
 
 
 def _fails(fn, *args):
@@ -147,3 +148,9 @@ def test_second_order_with_unit_spacing_is_caught(monkeypatch):
     monkeypatch.setattr(O, "second_order_images", lap1)
     _fails(TF.test_second_order_of_a_quadratic_and_a_ramp)
     _fails(TF.test_second_order_feature_layout_brute_force, np.random.default_rng(0))
+
+
+def test_horizontal_only_gradient_mass_is_caught(monkeypatch):
+    # the sampling mass taken from g_x alone
+    monkeypatch.setattr(O, "gradient_magnitude", lambda img: np.abs(O.gradient_images(img)[0]))
+    _fails(TS.test_a_single_bright_pixel_splits_the_draws_four_ways)
