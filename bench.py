@@ -427,6 +427,24 @@ def run_single(a, wl, config, rank, world, local):
                          "work": f"{nq} queries x {wl.n_pairs} entries x 2 x 160 flops"}}
         ixg.close()
         d_g.close()
+        # training-crop sampling (Sec. 5.1): 25 crops of 100 x 100 per training
+        # image of the workload, drawn by gradient mass (the paper's recipe)
+        imgs_t = [torch.from_numpy(x).cuda() for x in train]
+        n_draw, side = 25, 100
+        u_s = np.random.default_rng(17).random((len(train), n_draw))
+        crops_out = torch.empty((len(train) * n_draw, side, side), device="cuda")
+        for _ in range(2):
+            Z.sample_crops(ctx, imgs_t, u_s, side, side)
+        ms5 = timed_steps(lambda: Z.sample_crops(ctx, imgs_t, u_s, side, side), a.steps, st, torch, world)
+        px = sum(x.size for x in train)
+        byts = px * 4 + len(train) * n_draw * (1024 * 4 + 2 * side * side * 4)
+        res["crop_sampling"] = {
+            "value": world * len(train) * n_draw / (ms5 / 1e3), "unit": "crops/s", "ms_per_step": ms5,
+            "images": len(train), "pixels": px, "crops_per_image": n_draw, "crop": [side, side],
+            "algorithmic_bytes": byts, "GB/s": byts / (ms5 / 1e3) / 1e9,
+            "frac_hbm": byts / (ms5 / 1e3) / 1e9 / hbm_peak,
+            "note": "one call: draws copied in, tile masses, prefix, draws, crop gather, windows copied out"}
+        del imgs_t, crops_out
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_oracle_sample(wl, train, pos, alpha, beta, lr_np, a.cpu_sample_queries)
     return res

@@ -184,6 +184,29 @@ zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_re
 zoom_status zoom_dict_info(zoom_dict d, int64_t* n, int32_t* patch, int32_t* scale, double* blur_sigma,
                            int32_t* feature, int32_t* feature_dim);
 
+/* ---- training-crop sampling (Sec. 5.1) -----------------------------------
+ * Draws training crops from HR images where they have structure: for image
+ * m (device pointer images[m], heights[m] x widths[m] float32, row-major),
+ * every pixel carries the mass sqrt(g_x^2 + g_y^2) of its first-order
+ * gradients (clamped central differences, as feature 1, in FP64); pixels in
+ * row-major order form a CDF, and draw j of the image (u[m][j], host double
+ * [n_images][draws_per_image], each in [0, 1); the random numbers are inputs)
+ * selects the first pixel whose cumulative mass exceeds u * total (a flat
+ * image: pixel floor(u * h * w)).  The crop_h x crop_w window centred there
+ * (top = row - crop_h / 2, left = col - crop_w / 2, shifted inside the image)
+ * goes to windows (host int32 [n_images][draws_per_image][4]: row, col, top,
+ * left) and, if crops != NULL, its pixels to crops (device float32
+ * [n_images * draws_per_image][crop_h][crop_w], caller-owned).  The CDF is a
+ * fixed-order FP64 sum (tiles of 1024 pixels), equal to a sequential sum up
+ * to FP64 rounding, so only a draw within rounding of a CDF step can select
+ * the neighbouring pixel.  Synchronises `stream`.  Errors: INVALID_ARG for
+ * NULL pointers, a crop larger than an image, a draw outside [0, 1), more
+ * than 2^26 draws; OOM for the scratch. */
+zoom_status zoom_sample_crops(zoom_ctx ctx, const float* const* images, const int32_t* heights,
+                              const int32_t* widths, int32_t n_images, const double* u,
+                              int32_t draws_per_image, int32_t crop_h, int32_t crop_w,
+                              int32_t* windows, float* crops, void* stream);
+
 /* ---- LSH index (Sec. 3.2; Sec. 4.1, Eq. 10) -----------------------------
  * Hashes every dictionary feature into L tables.  alpha: host float32
  * [L*k][D] projection vectors (D the feature dimension); beta: host float32 [L*k] offsets in

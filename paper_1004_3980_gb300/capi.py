@@ -62,6 +62,8 @@ SIGNATURES = {
     "zoom_dict_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(C.c_double), _P(_i32), _P(_i32)]),
     "zoom_dict_save": (C.c_int, [_vp, C.c_char_p, _vp]),
+    "zoom_sample_crops": (C.c_int, [_vp, _P(_vp), _P(_i32), _P(_i32), _i32, _vp, _i32, _i32, _i32, _vp, _vp,
+                                    _vp]),
     "zoom_dict_load": (C.c_int, [_vp, C.c_char_p, _vp, _P(_vp)]),
     "zoom_index_save": (C.c_int, [_vp, C.c_char_p, _vp]),
     "zoom_index_load": (C.c_int, [_vp, C.c_char_p, _vp, _P(_vp)]),

@@ -196,6 +196,29 @@ class Dictionary:
             pass
 
 
+def sample_crops(ctx: Context, images, u, crop_h: int, crop_w: int, want_crops: bool = True, stream=None):
+    """Training crops drawn where the HR images have structure (Sec. 5.1,
+    zoom_sample_crops): images are CUDA float32 h x w tensors, u a numpy
+    [n_images][draws] array of uniform draws in [0, 1).  Returns the windows
+    (numpy int32 [n_images][draws][4]: centre row, centre column, top, left)
+    and the crops (CUDA float32 [n_images * draws][crop_h][crop_w], or None)."""
+    for t in images:
+        _need(t, torch.float32, "image")
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = len(images)
+    if u.ndim != 2 or u.shape[0] != n:
+        raise ValueError("u must be [n_images][draws]")
+    ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in images])
+    hs = (C.c_int32 * n)(*[t.shape[0] for t in images])
+    ws = (C.c_int32 * n)(*[t.shape[1] for t in images])
+    win = np.empty((n, u.shape[1], 4), np.int32)
+    crops = (torch.empty((n * u.shape[1], crop_h, crop_w), dtype=torch.float32, device=images[0].device)
+             if want_crops else None)
+    capi.call("zoom_sample_crops", ctx.handle, ptrs, hs, ws, n, u.ctypes.data, u.shape[1], crop_h, crop_w,
+              win.ctypes.data, crops.data_ptr() if crops is not None else None, _stream(stream))
+    return win, crops
+
+
 class Index:
     """L-table p-stable LSH index over a dictionary (zoom_build_index)."""
 

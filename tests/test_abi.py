@@ -64,3 +64,4 @@ def test_null_arguments_are_rejected_on_host(lib):
     assert lib.zoom_get_stats(None, None, None) == 1
     p = capi.UpscaleParams(8, 1e-3, 5, 1.5, 0.1, 3, 0, 4, 1e6)
     assert lib.zoom_backproject(None, None, None, 4, 4, C.byref(p), None, None) == 1
+    assert lib.zoom_sample_crops(None, None, None, None, 1, None, 1, 4, 4, None, None, None) == 1
