@@ -762,11 +762,12 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // queries (warps) per block: the staged rows of wide features (D = 50, two
 // buffers of 32 rows of 52 floats per warp) would exceed 48 KB of static
-// shared memory at four warps
+// shared memory at four warps.  Seven blocks of four warps fill the shared
+// memory at D <= 32 (73 registers a thread: no spills).
 __host__ __device__ constexpr int rerank_warps(int D) { return D > 32 ? 2 : 4; }
 
 template <int D, int MC>
-__global__ __launch_bounds__(rerank_warps(D) * 32, 8) void k_rerank(
+__global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank(
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
     const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
     const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
@@ -781,50 +782,62 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, 8) void k_rerank(
   // relative error of the FP32 difference-form distance of D terms
   constexpr float kRelD = D > 25 ? 8e-6f : 4e-6f;
   __shared__ float4 s_rows[kRerankWarps][2][32 * kRow4];
+  __shared__ uint64_t s_qk[kRerankWarps][32];   // the query's bucket keys (L <= 32)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (q >= nq) return;   // warp-uniform
-  float qv[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) qv[i] = qfeat[q * dpad + i];
+  if (lane < L) s_qk[wib][lane] = qkeys[q * L + lane];
+  // the query's feature in shared memory (read as 16-byte pieces beside the
+  // rows; registers stay free for the lists and the K best)
+  __shared__ float4 s_q4[kRerankWarps][kRow4];
+  if (lane < kRow4) s_q4[wib][lane] = reinterpret_cast<const float4*>(qfeat + q * dpad)[lane];
   const float qn = qn_arr[q];
   const float qnorm = sqrtf(qn);
-  // lane s < nsplit follows the list of split s
-  const bool lister = lane < nsplit;
-  const int64_t lbase = ((int64_t)(lister ? lane : 0) * nq + q) * MC;
-  int head = 0;
-  float hv = lister ? lm[lbase] : FLT_MAX;
-  float T = lister ? lm[lbase + MC - 1] : FLT_MAX;
+  // The chunk lists of every split sit in registers: lane j holds entry j of
+  // the list of split s in lv[s] / lcv[s] (FLT_MAX past nsplit or MC), and
+  // hd[s] (the same in every lane) is the split's next unexamined entry, so
+  // choosing the next chunk takes shuffles and no memory access.
+  constexpr int kMaxSplit = 8;
+  float lv[kMaxSplit];
+  int lcv[kMaxSplit], hd[kMaxSplit];
 #pragma unroll
-  for (int off = 16; off; off >>= 1) T = fminf(T, __shfl_xor_sync(kFull, T, off));
+  for (int s = 0; s < kMaxSplit; ++s) {
+    const bool has = s < nsplit && lane < MC;
+    const int64_t o = ((int64_t)s * nq + q) * MC + lane;
+    lv[s] = has ? lm[o] : FLT_MAX;
+    lcv[s] = has ? lc[o] : 0;
+    hd[s] = 0;
+  }
+  // T: the smallest list threshold (MC-th listed minimum) over the splits
+  float T = FLT_MAX;
+#pragma unroll
+  for (int s = 0; s < kMaxSplit; ++s)
+    if (s < nsplit) T = fminf(T, __shfl_sync(kFull, lv[s], MC - 1));
   // the listed chunk with the smallest minimum among the list heads (ties:
-  // lower split) and its index; -1 when the lists are exhausted
+  // lower split) and its split; -1 when the lists are exhausted
   auto peek = [&](float& best, int& bs) -> int {
-    best = hv;
-    bs = lane;
-    if (nsplit == 1) {
-      best = __shfl_sync(kFull, hv, 0);
-      bs = 0;
-    } else {
+    best = FLT_MAX;
+    bs = -1;
+    int ch = -1;
 #pragma unroll
-      for (int off = 16; off; off >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, best, off);
-        const int os = __shfl_xor_sync(kFull, bs, off);
-        if (ov < best || (ov == best && os < bs)) {
-          best = ov;
-          bs = os;
+    for (int s = 0; s < kMaxSplit; ++s) {
+      if (s < nsplit) {
+        const float v = __shfl_sync(kFull, lv[s], hd[s] & 31);
+        const int c = __shfl_sync(kFull, lcv[s], hd[s] & 31);
+        if (hd[s] < MC && v < best) {
+          best = v;
+          bs = s;
+          ch = c;
         }
       }
     }
-    if (best == FLT_MAX) return -1;
-    return __shfl_sync(kFull, lane == bs ? lc[lbase + head] : 0, bs);
+    return ch;
   };
   auto advance = [&](int bs) {
-    if (lane == bs) {
-      ++head;
-      hv = head < MC ? lm[lbase + head] : FLT_MAX;
-    }
+#pragma unroll
+    for (int s = 0; s < kMaxSplit; ++s)
+      if (s == bs) ++hd[s];
   };
   // the chunk's rows are contiguous: 16-byte asynchronous copies
   auto stage = [&](int c, int b) {
@@ -867,42 +880,37 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, 8) void k_rerank(
     if (lane < nrows) {
       const float4* srow = s_rows[wib][buf];
       dd = 0.f;
-      if constexpr (D <= 32) {
-        float x[kDP];
+      // each 16-byte piece is consumed as it is read (the order of i)
 #pragma unroll
-        for (int k = 0; k < kRow4; ++k) {
-          const float4 v4 = srow[lane * kRow4 + k];
-          x[4 * k] = v4.x;
-          x[4 * k + 1] = v4.y;
-          x[4 * k + 2] = v4.z;
-          x[4 * k + 3] = v4.w;
-        }
+      for (int k = 0; k < kRow4; ++k) {
+        const float4 v4 = srow[lane * kRow4 + k];
+        const float x4[4] = {v4.x, v4.y, v4.z, v4.w};
+        const float4 q4 = s_q4[wib][k];
+        const float qx4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-          const float df = qv[i] - x[i];
-          dd = fmaf(df, df, dd);
-        }
-      } else {
-        // wide rows: consume each 16-byte piece as it is read (same order)
-#pragma unroll
-        for (int k = 0; k < kRow4; ++k) {
-          const float4 v4 = srow[lane * kRow4 + k];
-          const float x4[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if (4 * k + t < D) {
-              const float df = qv[4 * k + t] - x4[t];
-              dd = fmaf(df, df, dd);
-            }
+        for (int t = 0; t < 4; ++t) {
+          if (4 * k + t < D) {
+            const float df = qx4[t] - x4[t];
+            dd = fmaf(df, df, dd);
           }
         }
       }
     }
-    // entries that could still enter the K best: LSH membership
+    // entries that could still enter the K best: LSH membership (the
+    // entry's keys eight tables at a time, loads issued together; stop at
+    // t hits)
     bool mem = false;
     if (dd != FLT_MAX && (members < K || dd < dK || (dd == dK && (int)e < iK))) {
+      const uint64_t* dk = dkeys + e * L;
+      const uint64_t* qk = s_qk[wib];
       int hits = 0;
-      for (int l = 0; l < L; ++l) hits += (qkeys[q * L + l] == dkeys[e * L + l]) ? 1 : 0;
+      for (int l0 = 0; l0 < L && hits < tmin; l0 += 8) {
+        uint64_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) kk[j] = l0 + j < L ? __ldg(dk + l0 + j) : 0ull;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hits += (l0 + j < L && kk[j] == qk[l0 + j]) ? 1 : 0;
+      }
       mem = hits >= tmin;
     }
     unsigned mm = __ballot_sync(kFull, mem);
