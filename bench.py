@@ -185,9 +185,11 @@ def cpu_oracle_sample(wl: S.Workload, train, pos, alpha, beta, lr, n_sample: int
 
 
 def launches_per_step(wl: S.Workload, tc: bool) -> int:
-    # features, hash, lookup, [operand, filter, rerank, re-run scan] or scan,
-    # LLE, overlap-add, 2 per back-projection step (+ a copy for odd counts)
-    return 3 + (4 if tc else 1) + 2 + 2 * wl.bp_iters
+    # features, hash, lookup; the exact tensor search: operand, single-term
+    # filter, rerank, then the second stage (gather, split operand, split
+    # filter, rerank) and the SIMT re-run (8), or the SIMT scan (1); LLE,
+    # overlap-add, 2 per back-projection step
+    return 3 + (8 if tc else 1) + 2 + 2 * wl.bp_iters
 
 
 def max_over_ranks(ms: float, world: int, device: str) -> float:
@@ -332,20 +334,22 @@ def run_single(a, wl, config, rank, world, local):
            "h2d_bytes_per_step": lr_host.numel() * 4, "d2h_bytes_per_step": hr_host.numel() * 4}
 
     # ---- rooflines ------------------------------------------------------------
-    d_feat = wl.patch ** 2
     filt_ms = stage.get("knn_filter_kernel", 0.0)
-    mma_flops = nq * wl.n_pairs * 2.0 * 80        # FP16 3-term split: K = 80 per (query, entry) pair
+    mma_flops = nq * wl.n_pairs * 2.0 * 32        # one FP16 term: K = 32 per (query, entry) pair
     achieved = mma_flops / (filt_ms / 1e3) / 1e12 if filt_ms > 0 else None
     traffic = profiled_traffic("paper_1004_3980_gb300/csrc/kernels_tc.cu",
-                               "profiles/knn_tc_exact_zoom2x_512_dict1m.md")
-    roofline = {"kernel": "k_knn_tc<10,16,0> (tcgen05 FP16-split distance filter)", "bound": "tensor",
-                "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                               "profiles/knn_tc_single_zoom2x_512_dict1m.md")
+    roofline = {"kernel": "k_knn_tc<4,16,0> (tcgen05 single-term FP16 distance filter of the exact form)",
+                "bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                 "frac": achieved / tc_peak if achieved else None, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                  "(profiles/knn_tc_exact_zoom2x_512_dict1m.md)",
+                                  "(profiles/knn_tc_single_zoom2x_512_dict1m.md)",
                 "peak_source": peak_src + ", bf16 dense (fp16 runs at the bf16 rate)",
-                "work": "258,064 queries x 1,000,000 entries x 2 x 80 flops (K = 80 per pair)",
-                "kernel_ms": filt_ms, "stage_share": filt_ms / ms_step if ms_step else None}
+                "work": "258,064 queries x 1,000,000 entries x 2 x 32 flops (K = 32 per pair)",
+                "kernel_ms": filt_ms, "stage_share": filt_ms / ms_step if ms_step else None,
+                "note": "at K = 32 a tile's MMAs take about as long as 40 % of its accumulator hand-off "
+                        "(TMEM loads and chunk minima), which sets the pace; the split filter alone "
+                        "(K = 80, key exact_split_filter) is tensor-bound"}
     PH2 = (wl.scale * wl.patch) ** 2
     oa_bytes = nq * wl.K * PH2 * 4 + hr_px * 4 + nq * (wl.K * 8 + 4)
     bp_bytes = wl.bp_iters * (hr_px * 4 * 3 + wl.lr_h * wl.lr_w * 4 * 3)
@@ -379,6 +383,27 @@ def run_single(a, wl, config, rank, world, local):
         rec = float(np.mean([len(np.intersect1d(qe[i], qb[i])) for i in range(len(qe))]) / wl.K)
         res["bf16"] = {"value": world * hr_px / 1e6 / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1,
                        "recall_vs_exact": rec, "psnr_vs_exact_db": 10 * np.log10(1.0 / max(mse, 1e-30))}
+        # the FP16-split filter alone (K = 80; the exact form's second stage)
+        p3 = params(search=3)
+        for _ in range(2):
+            Z.upscale(ix, lr, p3, out=out)
+        ms6 = timed_steps(lambda: Z.upscale(ix, lr, p3, out=out), a.steps, st, torch, world)
+        ctx.set_stage_timing(True)
+        f3 = []
+        for _ in range(3):
+            Z.upscale(ix, lr, p3, out=out)
+            f3.append(ctx.stats()["ms_stage"].get("knn_filter_kernel", 0.0))
+        ctx.set_stage_timing(False)
+        f3m = float(np.mean(f3))
+        ach3 = nq * wl.n_pairs * 2.0 * 80 / (f3m / 1e3) / 1e12 if f3m > 0 else None
+        res["exact_split_filter"] = {
+            "value": world * hr_px / 1e6 / (ms6 / 1e3), "unit": UNIT, "ms_per_step": ms6,
+            "identical_to_exact_form": bool(torch.equal(out, hr_exact)),
+            "roofline": {"kernel": "k_knn_tc<10,16,0> (FP16 hi/lo split, K = 80)", "bound": "tensor",
+                         "achieved": ach3, "peak": tc_peak, "unit": "TFLOP/s",
+                         "frac": ach3 / tc_peak if ach3 else None, "kernel_ms": f3m,
+                         "traffic": profiled_traffic("paper_1004_3980_gb300/csrc/kernels_tc.cu",
+                                                     "profiles/knn_tc_exact_zoom2x_512_dict1m.md")}}
         # one step of the plain SIMT scan (exact, no tensor cores)
         p2 = params(search=1)
         ms2 = timed_steps(lambda: Z.upscale(ix, lr, p2, out=out), 1, st, torch, world)
@@ -399,7 +424,8 @@ def run_single(a, wl, config, rank, world, local):
         # gradient features (Sec. 4.1): the same workload with the 2 P^2 = 50
         # first-order gradients of each LR patch as its feature; w = 8 puts
         # about the pixel form's share of the dictionary in the candidate set.
-        # Exact form: the FP16-split filter at K = 160.
+        # Exact form: the single-term FP16 filter at K = 64, the split filter
+        # (K = 160) as its second stage.
         d_g = Z.Dictionary(ctx, [torch.from_numpy(x).cuda() for x in train], pos, wl.scale, wl.patch,
                            wl.blur_sigma, feature=1)
         D_g = 2 * wl.patch ** 2
@@ -416,15 +442,15 @@ def run_single(a, wl, config, rank, world, local):
         ctx.set_stage_timing(False)
         st_g = ctx.stats()
         fg = float(np.mean(filt_g))
-        ach_g = nq * wl.n_pairs * 2.0 * 160 / (fg / 1e3) / 1e12 if fg > 0 else None
+        ach_g = nq * wl.n_pairs * 2.0 * 64 / (fg / 1e3) / 1e12 if fg > 0 else None
         res["gradient_features"] = {
             "value": world * hr_px / 1e6 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4,
             "feature_dim": D_g, "w": GRAD_W, "mean_bucket_sum_per_query": st_g["mean_bucket_sum"],
             "filter_fallback_queries": st_g["n_filter_fallback"],
-            "roofline": {"kernel": "k_knn_tc<20,16,0> (FP16 split, K = 160)", "bound": "tensor",
+            "roofline": {"kernel": "k_knn_tc<8,16,0> (single-term FP16, K = 64)", "bound": "tensor",
                          "achieved": ach_g, "peak": tc_peak, "unit": "TFLOP/s",
                          "frac": ach_g / tc_peak if ach_g else None, "kernel_ms": fg,
-                         "work": f"{nq} queries x {wl.n_pairs} entries x 2 x 160 flops"}}
+                         "work": f"{nq} queries x {wl.n_pairs} entries x 2 x 64 flops"}}
         ixg.close()
         d_g.close()
         # training-crop sampling (Sec. 5.1): 25 crops of 100 x 100 per training

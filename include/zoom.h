@@ -111,11 +111,14 @@ typedef struct {
  * FP32 exact rerank of those chunks' entries.
  * fp64_cond_threshold: the LLE solve runs in FP64 for a query whose
  * condition bound (trace(G) + eps) / eps exceeds it.
- * search (precision 0 only): 0 = automatic, 1 = SIMT scan of the dictionary
- * in FP32 difference form, 2 = tensor-core distance filter with a proven
- * exact FP32 rerank (queries it cannot settle re-run the SIMT scan).  All
- * three give the same neighbours.  Precision 1 always uses the tensor cores;
- * it needs rerank_mult * K <= 32. */
+ * search (precision 0 only): 0 = automatic (tensor cores from 4096
+ * dictionary entries), 1 = SIMT scan of the dictionary in FP32 difference
+ * form, 2 = tensor-core search with a proven exact FP32 rerank: a filter with
+ * one FP16 term per feature value (K = 32), then, for the queries its error
+ * bound cannot settle, the FP16 hi/lo-split filter (K = 80) on just those
+ * queries, then the SIMT scan for any left; 3 = the split filter alone (then
+ * the SIMT scan).  All four give the same neighbours bit for bit.  Precision 1
+ * always uses the tensor cores; it needs rerank_mult * K <= 32. */
 typedef struct {
   int32_t K;
   float reg_rel;
@@ -139,7 +142,9 @@ typedef struct {
   int64_t n_padded_queries; /* queries with fewer than K candidates (padded)  */
   int64_t n_fp64_solves;    /* LLE solves that ran in FP64                    */
   int64_t n_exact_match;    /* queries equal to a dictionary entry (one-hot)  */
-  int64_t n_filter_fallback;/* tensor-filter queries re-run on the exact path */
+  int64_t n_filter_fallback;/* queries the first tensor filter's rerank could
+                              * not settle (searched again: the split filter
+                              * after the single-term one, else the SIMT scan) */
   double ms_total;          /* device time of the last call (CUDA events)     */
   /* per-stage device milliseconds of the last call, when stage timing is on:
    * [0] features, [1] hashing, [2] bin lookup, [3] neighbour search,

@@ -265,7 +265,18 @@ struct TcArgs {
   // so the last round is shorter.  0: items are (split, pair) round robin.
   int tail_split;
   int full_rounds;
+  // nq_dev != nullptr: only the first min(*nq_dev, nq) queries are searched
+  // (a count written by an earlier kernel); nq stays the lists' row stride
+  const unsigned long long* nq_dev;
 };
+
+// Queries searched: nq, or the device count when one is given (read where
+// needed, so that nothing extra stays live in the roles' loops).
+__device__ __forceinline__ int64_t searched_queries(const TcArgs& a) {
+  if (!a.nq_dev) return a.nq;
+  const int64_t c = (int64_t)*a.nq_dev;
+  return c < a.nq ? c : a.nq;
+}
 
 // The work items of one CTA, in order; every role walks the same sequence.
 struct WorkIter {
@@ -273,6 +284,7 @@ struct WorkIter {
   // qp: query pair, seg: list index, [t0, t1): dictionary tiles
   __device__ bool next(const TcArgs& a, int& qp, int& seg, int& t0, int& t1) {
     const int G = gridDim.x, c = blockIdx.x;
+    const int nq_pairs = a.nq_dev ? (int)((searched_queries(a) + 2 * TC_ROWS - 1) / (2 * TC_ROWS)) : a.nq_pairs;
     if (a.tail_split > 0) {
       if (k < a.full_rounds) {
         qp = c + k * G;
@@ -280,7 +292,7 @@ struct WorkIter {
         t0 = 0;
         t1 = a.nd_tiles;
       } else {
-        const int tail = a.nq_pairs - a.full_rounds * G;
+        const int tail = nq_pairs - a.full_rounds * G;
         const int j = c + (k - a.full_rounds) * G;   // tail item: part j / tail of pair j % tail
         if (j >= tail * a.tail_split) return false;
         qp = a.full_rounds * G + j % tail;
@@ -290,9 +302,9 @@ struct WorkIter {
       }
     } else {
       const int item = c + k * G;
-      if (item >= a.nsplit * a.nq_pairs) return false;
-      seg = item / a.nq_pairs;
-      qp = item % a.nq_pairs;
+      if (item >= a.nsplit * nq_pairs) return false;
+      seg = item / nq_pairs;
+      qp = item % nq_pairs;
       t0 = seg * a.tiles_per_split;
       t1 = min(a.nd_tiles, t0 + a.tiles_per_split);
     }
@@ -500,7 +512,7 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
     while (it.next(a, qp, split, t0, t1)) {
       if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
       const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
-      const bool valid = q < a.nq;
+      const bool valid = q < searched_queries(a);
       const float qn = valid ? a.qn[q] : 0.f;
       float ld[MC];
       int li[MC];
@@ -600,11 +612,13 @@ __device__ __forceinline__ uint16_t b_bits(__nv_bfloat16 h) { return __bfloat16_
 // and the norm pair sits at 3S (S = 25 for K = 80, 50 for K = 160).
 template <int D, int KC>
 __global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
-                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
+                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out,
+                                const unsigned long long* __restrict__ n_dev) {
   constexpr int S = KC * 5 / 2;
   static_assert(D <= S && 3 * S + 2 <= KC * 8, "operand layout");
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
+  if (n_dev && (int64_t)*n_dev < n) n = (int64_t)*n_dev;   // rows past a device count are padding
   uint16_t row[KC * 8];
 #pragma unroll
   for (int k = 0; k < KC * 8; ++k) row[k] = 0;
@@ -652,10 +666,12 @@ __global__ void k_operand_f16x3(const float* __restrict__ feat, int dpad, int64_
 
 template <int D, int KC>
 __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
-                               int role, uint16_t* __restrict__ op, float* __restrict__ norm_out) {
+                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out,
+                                const unsigned long long* __restrict__ n_dev) {
   static_assert(D + 3 <= KC * 8, "operand layout");
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
+  if (n_dev && (int64_t)*n_dev < n) n = (int64_t)*n_dev;   // rows past a device count are padding
   uint16_t row[KC * 8];
 #pragma unroll
   for (int k = 0; k < KC * 8; ++k) row[k] = 0;
@@ -681,6 +697,55 @@ __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t
     if (norm_out) norm_out[r] = n2;
   } else if (role == 1) {
     row[D] = b_bits(__float2bfloat16_rn(60000.f));
+  }
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) {
+    uint4 pk;
+    pk.x = (uint32_t)row[kc * 8 + 0] | ((uint32_t)row[kc * 8 + 1] << 16);
+    pk.y = (uint32_t)row[kc * 8 + 2] | ((uint32_t)row[kc * 8 + 3] << 16);
+    pk.z = (uint32_t)row[kc * 8 + 4] | ((uint32_t)row[kc * 8 + 5] << 16);
+    pk.w = (uint32_t)row[kc * 8 + 6] | ((uint32_t)row[kc * 8 + 7] << 16);
+    *reinterpret_cast<uint4*>(op + op_off(r, kc * 8, KC)) = pk;
+  }
+}
+
+// Exact form with one FP16 term (K = 32, or 64 for D = 50): A [q | 1 1 1],
+// B [-2c | n1 n2 n3] with ||c||^2 as three FP16 terms; acc misses the
+// rounding of q and c to FP16 (2^-11 relative each), which the rerank's
+// bound covers (2^-9 ||q|| r).
+template <int D, int KC>
+__global__ void k_operand_f16s(const float* __restrict__ feat, int dpad, int64_t n, int64_t n_rows,
+                                int role, uint16_t* __restrict__ op, float* __restrict__ norm_out,
+                                const unsigned long long* __restrict__ n_dev) {
+  static_assert(D + 3 <= KC * 8, "operand layout");
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  if (n_dev && (int64_t)*n_dev < n) n = (int64_t)*n_dev;   // rows past a device count are padding
+  uint16_t row[KC * 8];
+#pragma unroll
+  for (int k = 0; k < KC * 8; ++k) row[k] = 0;
+  if (r < n) {
+    float n2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float v = feat[r * dpad + i];
+      n2 = fmaf(v, v, n2);
+      row[i] = h_bits(__float2half_rn(role == 0 ? v : -2.f * v));
+    }
+    if (role == 0) {
+      row[D] = row[D + 1] = row[D + 2] = h_bits(__float2half_rn(1.f));
+    } else {
+      const __half n1 = __float2half_rn(n2);
+      const float r1 = n2 - __half2float(n1);
+      const __half nb = __float2half_rn(r1);
+      const __half nc = __float2half_rn(r1 - __half2float(nb));
+      row[D] = h_bits(n1);
+      row[D + 1] = h_bits(nb);
+      row[D + 2] = h_bits(nc);
+    }
+    if (norm_out) norm_out[r] = n2;
+  } else if (role == 1) {
+    row[D] = h_bits(__float2half_rn(60000.f));
   }
 #pragma unroll
   for (int kc = 0; kc < KC; ++kc) {
@@ -771,9 +836,10 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
     const float* __restrict__ qfeat, int dpad, const float* __restrict__ qn_arr,
     const uint64_t* __restrict__ qkeys, int64_t nq, const float* __restrict__ dfeat,
     const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
-    const int32_t* __restrict__ lc, int nsplit, int K, int exact, float c_qr, float c_sq,
+    const int32_t* __restrict__ lc, int nsplit, int K, int exact, float c_qr, float c_sq, float c_abs,
     int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ fb_list,
-    unsigned long long* __restrict__ counters) {
+    unsigned long long* __restrict__ counters, int fb_slot, const int32_t* __restrict__ qmap,
+    const unsigned long long* __restrict__ nq_dev) {
   constexpr int kDP = (D + 3) / 4 * 4;   // feature row stride (floats)
   constexpr int kRow4 = kDP / 4;         // 16-byte pieces per row
   // two buffers per warp: the next chunk's rows arrive (cp.async) while the
@@ -786,7 +852,9 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (q >= nq) return;   // warp-uniform
+  if (q >= nq || (nq_dev && q >= (int64_t)*nq_dev)) return;   // warp-uniform
+  // query q of this launch is query oq of the call (qmap: a compacted subset)
+  const int64_t oq = qmap ? qmap[q] : q;
   if (lane < L) s_qk[wib][lane] = qkeys[q * L + lane];
   // the query's feature in shared memory (read as 16-byte pieces beside the
   // rows; registers stay free for the lists and the K best)
@@ -960,7 +1028,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
       iK = __shfl_sync(kFull, bi, K - 1);
       // an entry that could beat dK has ||c|| <= ||q|| + sqrt(dK)
       const float rc = qnorm + sqrtf(dK) * 1.001f + 1e-6f;
-      delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + kRelD * dK + 1e-12f;
+      delta = c_qr * qnorm * rc + c_sq * (rc * rc + qn) + kRelD * dK + c_abs * (qnorm + rc) + 1e-12f;
     }
     // stop once no entry of a further chunk can beat the K-th member
     if (nchunk < 0 || (members >= K && nbest - delta > dK)) break;
@@ -972,15 +1040,37 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
   const bool flagged = members < K || (exact && !(T - delta > dK));
   if (flagged) {
     if (lane == 0) {
-      const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
-      fb_list[slot] = (int32_t)q;
+      const unsigned long long slot = atomicAdd(&counters[fb_slot], 1ull);
+      fb_list[slot] = (int32_t)oq;
     }
     return;
   }
   if (lane < K) {
-    nbr[q * K + lane] = bi;
-    dist[q * K + lane] = bd;
+    nbr[oq * K + lane] = bi;
+    dist[oq * K + lane] = bd;
   }
+}
+
+// Compacts the queries listed in idx[0 .. min(*count, cap)) -- their
+// features and bucket keys -- for a second search; listed queries at or past
+// cap go to the list `over` (count at counters[over_slot]).  One thread per
+// listed query.
+__global__ void k_gather_queries(const int32_t* __restrict__ idx, const unsigned long long* __restrict__ count,
+                                 int64_t cap, const float* __restrict__ feat, int dpad,
+                                 const uint64_t* __restrict__ keys, int L, float* __restrict__ cfeat,
+                                 uint64_t* __restrict__ ckeys, int32_t* __restrict__ over,
+                                 unsigned long long* __restrict__ counters, int over_slot) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (int64_t)*count) return;
+  const int64_t q = idx[j];
+  if (j >= cap) {
+    const unsigned long long slot = atomicAdd(&counters[over_slot], 1ull);
+    over[slot] = (int32_t)q;
+    return;
+  }
+  for (int i = 0; i < dpad; i += 4)
+    *reinterpret_cast<float4*>(cfeat + j * dpad + i) = *reinterpret_cast<const float4*>(feat + q * dpad + i);
+  for (int l = 0; l < L; ++l) ckeys[j * L + l] = keys[q * L + l];
 }
 
 }  // namespace
@@ -998,20 +1088,24 @@ int64_t tc_rows_padded(int64_t n, bool even_tiles) {
 
 int tc_kc(int d, int precision) {
   if (precision == 0) return d <= 25 ? 10 : 20;
-  return d + 3 <= 32 ? 4 : 8;
+  return d + 3 <= 32 ? 4 : 8;   // BF16 and single-term FP16
 }
 
 cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
-                           int precision, uint16_t* op, float* norm_out, cudaStream_t st) {
+                           int precision, uint16_t* op, float* norm_out, cudaStream_t st,
+                           const unsigned long long* n_dev) {
   const int blocks = (int)((n_rows + 127) / 128);
 #define ZOOM_OP(DD)                                                                                  \
   do {                                                                                               \
     if (precision == 0)                                                                              \
       k_operand_f16x3<DD, (DD <= 25 ? 10 : 20)><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, \
-                                                                         norm_out);                  \
-    else                                                                                             \
+                                                                         norm_out, n_dev);           \
+    else if (precision == 1)                                                                         \
       k_operand_bf16<DD, (DD + 3 <= 32 ? 4 : 8)><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, \
-                                                                          norm_out);                 \
+                                                                          norm_out, n_dev);          \
+    else                                                                                             \
+      k_operand_f16s<DD, (DD + 3 <= 32 ? 4 : 8)><<<blocks, 128, 0, st>>>(feat, dpad, n, n_rows, role, op, \
+                                                                          norm_out, n_dev);          \
   } while (0)
   switch (d) {
     case 9: ZOOM_OP(9); break;
@@ -1030,7 +1124,7 @@ size_t tc_smem_bytes(int KC) {
 }
 
 int tc_list_size(int precision, int K, int rerank_mult) {
-  if (precision == 0) return K <= 12 ? 16 : 32;
+  if (precision != 1) return K <= 12 ? 16 : 32;
   return rerank_mult * K <= 16 ? 16 : 32;
 }
 
@@ -1045,12 +1139,15 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
 
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
                           int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
-                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st) {
+                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st,
+                          const unsigned long long* nq_dev) {
   TcArgs a;
   a.qop = qop;
   a.qn = qn;
   a.dop = dop;
   a.nq = nq;
+  a.nq_dev = nq_dev;
+  if (nq_dev && tail_split > 0) return cudaErrorInvalidValue;   // the tail split needs the count on the host
   a.nd = nd;
   a.nq_pairs = (int)((nq + 2 * TC_ROWS - 1) / (2 * TC_ROWS));
   a.nd_tiles = (int)((nd + TC_ROWS - 1) / TC_ROWS);
@@ -1070,6 +1167,8 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
   return MC == 16 ? run_tc_kernel<KC, 16, T>(a, grid, smem, st) : run_tc_kernel<KC, 32, T>(a, grid, smem, st)
   if (precision == 0 && kc == 10) ZOOM_TC(10, 0);
   if (precision == 0 && kc == 20) ZOOM_TC(20, 0);
+  if (precision == 2 && kc == 4) ZOOM_TC(4, 0);
+  if (precision == 2 && kc == 8) ZOOM_TC(8, 0);
   if (precision == 1 && kc == 4) ZOOM_TC(4, 1);
   if (precision == 1 && kc == 8) ZOOM_TC(8, 1);
 #undef ZOOM_TC
@@ -1080,37 +1179,49 @@ template <int D, int MC>
 static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn, const uint64_t* qkeys,
                             int64_t nq, const float* dfeat, const uint64_t* dkeys, int64_t nd, int L,
                             int tmin, const float* ld, const int32_t* li, int nsplit, int exact, float c_qr,
-                            float c_sq, int32_t* nbr, float* dist, int32_t* fb,
-                            unsigned long long* counters, cudaStream_t st) {
+                            float c_sq, float c_abs, int32_t* nbr, float* dist, int32_t* fb,
+                            unsigned long long* counters, int fb_slot, const int32_t* qmap,
+                            const unsigned long long* nq_dev, cudaStream_t st) {
   constexpr int kRerankWarps = rerank_warps(D);
   const int64_t blocks = (nq + kRerankWarps - 1) / kRerankWarps;   // one warp per query
   k_rerank<D, MC><<<(unsigned)blocks, kRerankWarps * 32, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
-                                                    li, nsplit, K, exact, c_qr, c_sq, nbr, dist, fb, counters);
+                                                    li, nsplit, K, exact, c_qr, c_sq, c_abs, nbr, dist, fb,
+                                                    counters, fb_slot, qmap, nq_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int exact, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
-                          cudaStream_t st) {
-  if (nsplit > 8 || K < 1 || K > 16 || dpad != (d + 3) / 4 * 4) return cudaErrorInvalidValue;
+                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
+                          cudaStream_t st, int fb_slot, const int32_t* qmap, const unsigned long long* nq_dev) {
+  if (nsplit > 8 || K < 1 || K > 16 || dpad != (d + 3) / 4 * 4 || form < 0 || form > 2)
+    return cudaErrorInvalidValue;
   if (nq == 0) return cudaSuccess;
-  // |d~ - d| <= c_qr ||q|| r + c_sq (r^2 + ||q||^2) + 4e-6 d for an entry with
-  // ||c|| <= r.  Exact form: FP16 hi/lo split (the dropped q_lo.c_lo term and
-  // the rounding of the split, within 6 * 2^-16 ||q|| r), FP32 accumulation
-  // of 80 terms and the FP32 rerank (2^-16 (r^2 + ||q||^2), 4e-6 d).  BF16
-  // form: each operand rounded to 8 significant bits (2 * 2^-8 ||q|| r for
-  // the product term), 32 FP32 accumulations; used only to stop examining.
-  // Twice the operand width (gradient features of 5 x 5 patches, K = 160
-  // or 64) doubles the accumulation terms: the coefficients are doubled (the
-  // kernel doubles the relative term of its FP32 rerank for D > 25 too).
-  const float wide = tc_kc(d, exact ? 0 : 1) > (exact ? 10 : 4) ? 2.f : 1.f;
-  const float c_qr = wide * (exact ? 6.f / 65536.f : 1.05f / 128.f);
-  const float c_sq = wide * (exact ? 1.f / 65536.f : 1.f / 262144.f);
+  // |d~ - d| <= c_qr ||q|| r + c_sq (r^2 + ||q||^2) + c_abs (||q|| + r)
+  // + 4e-6 d for an entry with ||c|| <= r.  form 1 (FP16 hi/lo split): the
+  // dropped q_lo.c_lo term and the rounding of the split, within
+  // 6 * 2^-16 ||q|| r, FP32 accumulation of 80 terms and the FP32 rerank
+  // (2^-16 (r^2 + ||q||^2), 4e-6 d).  form 2 (one FP16 term): q and c each
+  // rounded to 11 significant bits, 2 (2^-10 + 2^-22) ||q|| r for the
+  // product term (Cauchy-Schwarz), 1.05 * 2^-9 with the accumulation of 32
+  // terms.  Both: FP16 subnormals round with an absolute error up to 2^-25
+  // per element, 2 * 2^-25 * sum(|q_i| + |c_i|) <= 2^-23 sqrt(D) (||q|| + r)
+  // with slack.  form 0 (BF16): each operand rounded to 8 significant bits
+  // (2 * 2^-8 ||q|| r for the product term), 32 FP32 accumulations; used only
+  // to stop examining (no proof).  Twice the operand width (gradient
+  // features of 5 x 5 patches, K = 160 or 64) doubles the accumulation
+  // terms: the coefficients are doubled (the kernel doubles the relative
+  // term of its FP32 rerank for D > 25 too).
+  const int prec = form == 1 ? 0 : (form == 0 ? 1 : 2);
+  const float wide = tc_kc(d, prec) > (prec == 0 ? 10 : 4) ? 2.f : 1.f;
+  const float c_qr = wide * (form == 1 ? 6.f / 65536.f : form == 2 ? 1.05f / 512.f : 1.05f / 128.f);
+  const float c_sq = wide * (form == 0 ? 1.f / 262144.f : 1.f / 65536.f);
+  const float c_abs = 1.1920929e-07f * sqrtf((float)d);   // 2^-23 sqrt(D)
+  const int exact = form != 0;
 #define ZOOM_RR(DD, MM)                                                                          \
   return rerank_k<DD, MM>(K, qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld, li, nsplit, \
-                          exact, c_qr, c_sq, nbr, dist, fb, counters, st)
+                          exact, c_qr, c_sq, c_abs, nbr, dist, fb, counters, fb_slot, qmap, nq_dev, st)
   if (d == 25 && MC == 16) ZOOM_RR(25, 16);
   if (d == 25 && MC == 32) ZOOM_RR(25, 32);
   if (d == 9 && MC == 16) ZOOM_RR(9, 16);
@@ -1121,4 +1232,15 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
   if (d == 50 && MC == 32) ZOOM_RR(50, 32);
 #undef ZOOM_RR
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gather_queries(const int32_t* idx, const unsigned long long* count, int64_t max_count,
+                                  int64_t cap, const float* feat, int dpad, const uint64_t* keys, int L,
+                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* counters,
+                                  int over_slot, cudaStream_t st) {
+  if (max_count == 0) return cudaSuccess;
+  if (dpad % 4) return cudaErrorInvalidValue;
+  k_gather_queries<<<(unsigned)((max_count + 127) / 128), 128, 0, st>>>(idx, count, cap, feat, dpad, keys, L,
+                                                                         cfeat, ckeys, over, counters, over_slot);
+  return cudaGetLastError();
 }

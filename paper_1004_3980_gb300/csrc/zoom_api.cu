@@ -108,7 +108,7 @@ bool check_upscale_params(const zoom_upscale_params* p, zoom_dict d, std::string
   if (p->precision == 1 && (p->rerank_mult < 1 || p->rerank_mult * p->K > 32)) {
     why = "rerank_mult * K must be in K..32"; return false;
   }
-  if (p->search < 0 || p->search > 2) { why = "search must be 0, 1 or 2"; return false; }
+  if (p->search < 0 || p->search > 3) { why = "search must be 0, 1, 2 or 3"; return false; }
   return true;
 }
 
@@ -396,6 +396,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     c.take<int32_t>(L);
     c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 0) * 8);
     c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 1) * 8);
+    c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 2) * 8);
     ix->bytes = c.off + 256;
   }
   void* mem = zoom_alloc(ctx, ix->bytes, st);
@@ -413,6 +414,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->nuniq = c.take<int32_t>(L);
   ix->dop16 = c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 0) * 8);
   ix->dopbf = c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 1) * 8);
+  ix->dopf1 = c.take<uint16_t>(ix->nd_rows * tc_kc(d->d, 2) * 8);
   zoom_status rc = ZOOM_OK;
   cudaError_t e = cudaMemcpyAsync(ix->alpha, alpha, (size_t)L * k * d->d * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ix->beta, beta, (size_t)L * k * 4, cudaMemcpyHostToDevice, st);
@@ -422,6 +424,8 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 0, ix->dop16, nullptr, st);
   if (e == cudaSuccess)
     e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 1, ix->dopbf, nullptr, st);
+  if (e == cudaSuccess)
+    e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 2, ix->dopf1, nullptr, st);
   if (e == cudaSuccess) {
     Scratch scr(ctx, st);
     size_t sb = csr_scratch_bytes(N);
@@ -486,6 +490,10 @@ struct SearchPlan {
   int tail_split = 0;     // > 0: whole pairs, then the last round's pairs cut in parts
   int prec = 0, MC = 16, nsplit = 1, KCH = 80;
   int64_t q_rows = 0;
+  // precision 2: the queries the single-term filter cannot settle (at most
+  // cap2) run again through the FP16-split filter, nsplit2 dictionary parts
+  int64_t cap2 = 0, q_rows2 = 0;
+  int MC2 = 16, nsplit2 = 1;
   size_t bytes = 0;
 };
 
@@ -501,9 +509,11 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
     p.bytes = c.off + 256;
     return p;
   }
-  p.tc = prm->precision == 1 || prm->search == 2 || (prm->search == 0 && d->n >= 4096);
+  p.tc = prm->precision == 1 || prm->search >= 2 || (prm->search == 0 && d->n >= 4096);
   if (!p.tc) return p;
-  p.prec = prm->precision;
+  // the exact form: the single-term FP16 filter with the split-filter second
+  // stage (internal precision 2), or the split filter alone (search 3)
+  p.prec = prm->precision == 1 ? 1 : (prm->search == 3 ? 0 : 2);
   p.MC = mc_override > 0 ? mc_override : tc_list_size(p.prec, prm->K, prm->rerank_mult);
   const int64_t nd_tiles = ix->nd_rows / 128;
   const int64_t nq_pairs = (nq + 255) / 256;
@@ -552,12 +562,27 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   p.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
   p.q_rows = tc_rows_padded(nq, true);
   p.KCH = tc_kc(d->d, p.prec) * 8;
+  if (p.prec == 2) {
+    p.cap2 = std::min<int64_t>(nq, 8192);
+    p.q_rows2 = tc_rows_padded(p.cap2, true);
+    p.MC2 = tc_list_size(0, prm->K, prm->rerank_mult);
+    p.nsplit2 = (int)std::min<int64_t>(8, nd_tiles);
+  }
   Carver c(nullptr);
   c.take<uint16_t>(p.q_rows * p.KCH);
   c.take<float>(nq);
   c.take<float>((size_t)p.nsplit * nq * p.MC);
   c.take<int32_t>((size_t)p.nsplit * nq * p.MC);
   c.take<int32_t>(nq);
+  if (p.prec == 2) {
+    c.take<float>((size_t)p.cap2 * d->dpad);
+    c.take<uint64_t>((size_t)p.cap2 * ix->L);
+    c.take<uint16_t>((size_t)p.q_rows2 * tc_kc(d->d, 0) * 8);
+    c.take<float>(p.cap2);
+    c.take<float>((size_t)p.nsplit2 * p.cap2 * p.MC2);
+    c.take<int32_t>((size_t)p.nsplit2 * p.cap2 * p.MC2);
+    c.take<int32_t>(nq);
+  }
   p.bytes = c.off + 256;
   return p;
 }
@@ -592,16 +617,46 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
   zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
-    e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : ix->dopbf, d->n, pl.prec, pl.KCH / 8, pl.MC,
+    e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : pl.prec == 1 ? ix->dopbf : ix->dopf1, d->n, pl.prec,
+                      pl.KCH / 8, pl.MC,
                       pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
-                      ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : 0, b.nbr, b.dist, fb, ctx->d_counters,
-                      st);
+                      ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : (pl.prec == 1 ? 0 : 2), b.nbr, b.dist, fb,
+                      ctx->d_counters, st);
+  const unsigned long long* n_fb = ctx->d_counters + CNT_FALLBACK;
+  if (pl.prec == 2) {
+    // second stage, on the device's count of unsettled queries: compact
+    // them, FP16-split operands, the split filter over nsplit2 parts, its
+    // rerank (results written at the original query indices); what it
+    // cannot settle joins fb2 for the SIMT scan
+    float* cfeat = s2.take<float>((size_t)pl.cap2 * d->dpad);
+    uint64_t* ckeys = s2.take<uint64_t>((size_t)pl.cap2 * ix->L);
+    uint16_t* cqop = s2.take<uint16_t>((size_t)pl.q_rows2 * tc_kc(d->d, 0) * 8);
+    float* cqn = s2.take<float>(pl.cap2);
+    float* ld2 = s2.take<float>((size_t)pl.nsplit2 * pl.cap2 * pl.MC2);
+    int32_t* li2 = s2.take<int32_t>((size_t)pl.nsplit2 * pl.cap2 * pl.MC2);
+    int32_t* fb2 = s2.take<int32_t>(nq);
+    if (e == cudaSuccess)
+      e = launch_gather_queries(fb, n_fb, nq, pl.cap2, b.feat, d->dpad, b.keys, ix->L, cfeat, ckeys, fb2,
+                                ctx->d_counters, CNT_FALLBACK2, st);
+    if (e == cudaSuccess)
+      e = launch_operand(cfeat, d->dpad, d->d, pl.cap2, pl.q_rows2, 0, 0, cqop, cqn, st, n_fb);
+    if (e == cudaSuccess)
+      e = launch_knn_tc(cqop, cqn, pl.cap2, ix->dop16, d->n, 0, tc_kc(d->d, 0), pl.MC2, pl.nsplit2, 0, ctx->n_sm,
+                        ld2, li2, ctx->d_status, st, n_fb);
+    if (e == cudaSuccess)
+      e = launch_rerank(d->d, pl.MC2, K, cfeat, d->dpad, cqn, ckeys, pl.cap2, d->feat, ix->dkeys, d->n, ix->L,
+                        ix->t, ld2, li2, pl.nsplit2, 1, b.nbr, b.dist, fb2, ctx->d_counters, st, CNT_FALLBACK2, fb,
+                        n_fb);
+    if (e == cudaSuccess)
+      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb2,
+                           ctx->d_counters + CNT_FALLBACK2, st);
+    return e;
+  }
   if (e == cudaSuccess)
-    e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
-                         ctx->d_counters + CNT_FALLBACK, st);
+    e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb, n_fb, st);
   return e;
 }
 
@@ -958,7 +1013,7 @@ zoom_status autotune_group(Group& g, const zoom_upscale_params* prm, cudaStream_
   const int mc0 = tc_list_size(prm->precision, prm->K, prm->rerank_mult);
   for (int s : {0, 1, 2, 4}) {
     cands.push_back({s, mc0});
-    if (prm->precision == 0 && mc0 == 16) cands.push_back({s, 32});
+    if (prm->precision != 1 && mc0 == 16) cands.push_back({s, 32});
   }
   TuneChoice best;
   best.ms = 1e30f;

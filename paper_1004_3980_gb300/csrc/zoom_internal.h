@@ -19,6 +19,7 @@ enum CounterSlot {
   CNT_FP64 = 4,         // LLE solves in FP64
   CNT_EXACT = 5,        // exact-match (one-hot) queries
   CNT_FALLBACK = 6,     // tensor-filter queries re-run exactly
+  CNT_FALLBACK2 = 7,    // queries the second (FP16-split) filter left to the SIMT scan
   CNT_N = 8
 };
 
@@ -76,6 +77,7 @@ struct zoom_index_s {
   // tensor-core operands of the dictionary: 128-row tiles [tile][kc][128][8]
   uint16_t* dop16 = nullptr; // FP16 3-term split, tc_kc(d, 0) chunks of 8 per row
   uint16_t* dopbf = nullptr; // BF16 single term, tc_kc(d, 1) chunks of 8 per row
+  uint16_t* dopf1 = nullptr; // FP16 single term, tc_kc(d, 2) chunks of 8 per row
   int64_t nd_rows = 0;       // rows of the operands (N rounded up to 128)
   size_t bytes = 0;
 };
@@ -140,10 +142,13 @@ cudaError_t launch_lle_grad(zoom_dict d, const float* qfeat, int64_t nq, const i
 
 // tensor-core neighbour search (kernels_tc.cu)
 int64_t tc_rows_padded(int64_t n, bool even_tiles);
+// n_dev: rows at or past min(*n_dev, n) are padding (a count on the device)
 cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_t n_rows, int role,
-                           int precision, uint16_t* op, float* norm_out, cudaStream_t st);
+                           int precision, uint16_t* op, float* norm_out, cudaStream_t st,
+                           const unsigned long long* n_dev = nullptr);
 // operand width in 8-element chunks for feature dimension d: FP16 split
-// (precision 0) 10 (K = 80, d <= 25) or 20 (K = 160, d = 50); BF16 4 or 8
+// (precision 0) 10 (K = 80, d <= 25) or 20 (K = 160, d = 50); BF16
+// (precision 1) and single-term FP16 (precision 2) 4 or 8
 int tc_kc(int d, int precision);
 size_t tc_smem_bytes(int KC);
 int tc_list_size(int precision, int K, int rerank_mult);
@@ -152,15 +157,26 @@ int tc_list_size(int precision, int K, int rerank_mult);
 // equal tail_split); 0: nsplit round-robin splits of every pair
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
                           int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
-                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st);
+                          float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st,
+                          const unsigned long long* nq_dev = nullptr);
 // ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
-// chunk index), ascending; exact = 1 for the FP16-split filter (proof and
-// fallback flags), 0 for the BF16 filter.
+// chunk index), ascending; form 1 for the FP16-split filter, 2 for the
+// single-term FP16 filter (both: proof and fallback flags), 0 for the BF16
+// filter.  Queries it cannot settle are appended to fb (count at
+// counters[fb_slot]); with qmap, query q of this launch is query qmap[q] of
+// the call (outputs and fb use the latter) and only q < *nq_dev run.
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int exact, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
-                          cudaStream_t st);
+                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
+                          cudaStream_t st, int fb_slot = CNT_FALLBACK, const int32_t* qmap = nullptr,
+                          const unsigned long long* nq_dev = nullptr);
+// The queries idx[0 .. *count) (count <= max_count), compacted: features and
+// keys of the first cap into cfeat / ckeys, the rest appended to `over`.
+cudaError_t launch_gather_queries(const int32_t* idx, const unsigned long long* count, int64_t max_count,
+                                  int64_t cap, const float* feat, int dpad, const uint64_t* keys, int L,
+                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* counters,
+                                  int over_slot, cudaStream_t st);
 
 // backward / adjoint steps (kernels_backward.cu) and the key sort (kernels_build.cu)
 cudaError_t sort_keys_csr(const int32_t* keys32, int64_t n, int32_t* sorted_pos, uint64_t* ukeys,

@@ -1,7 +1,9 @@
-"""Tensor-core neighbour search (tcgen05): the FP16-split filter with its
-exact FP32 rerank must return exactly the neighbours of the SIMT scan (both
-follow the same (member, distance, ID) order), and the BF16 precision form
-must keep its recall against exact search."""
+"""Tensor-core neighbour search (tcgen05): the exact form -- the single-term
+FP16 filter with its proven FP32 rerank, the FP16-split filter as its
+second stage, and the split filter alone -- must return exactly the
+neighbours of the SIMT scan (all follow the same (member, distance, ID)
+order), and the BF16 precision form must keep its recall against exact
+search."""
 import numpy as np
 import pytest
 
@@ -93,3 +95,48 @@ def test_bf16_precision_form_recall_and_psnr(small, rerank_mult):
     mse = float(np.mean((hr - x) ** 2))
     psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
     assert psnr >= 50.0, psnr
+
+
+@pytest.mark.parametrize("K", [5, 16])
+def test_split_filter_alone_equals_scan(small, K):
+    case, ctx, d, ix = small
+    wl = case.wl
+    lr = case.lr[:45, :61]
+    a = _query(ix, lr, wl, search=1, K=K)
+    b = _query(ix, lr, wl, search=3, K=K)
+    ctx.sync_status()
+    assert (a["nbr"] == b["nbr"]).all() and (a["dist"] == b["dist"]).all()
+
+
+@pytest.mark.parametrize("sigma", [0.012, 0.006], ids=["second_stage", "third_stage"])
+def test_later_stages_settle_what_the_single_term_filter_cannot(sigma):
+    # The dictionary is one mosaic of 32 noisy copies of the test image side
+    # by side: IDs run along the mosaic's rows, so a query's 32 near
+    # duplicates fall in 32 different chunks of the same dictionary split,
+    # within the single-term filter's error bound of one another.  Nearly
+    # every query then fails that filter's proof (CPU simulation of the
+    # proof with the planner's 8 splits: 96 %, resp. 99 %) and goes to the
+    # split filter; with the smaller noise 40 % fail that proof too and go to
+    # the SIMT scan.  The result must be the SIMT scan's.
+    import paper_1004_3980_gb300 as Z
+    s, P, n_copies = 2, 5, 32
+    hr = S.make_image(91, 80, 88).astype(np.float64)
+    lr = O.degrade(hr, s, 0.8).astype(np.float32)
+    g = np.random.default_rng(4)
+    mosaic = np.concatenate([np.clip(hr + g.normal(scale=sigma, size=hr.shape), 0, 1) for _ in range(n_copies)],
+                            axis=1).astype(np.float32)
+    lh, lw = mosaic.shape[0] // s, mosaic.shape[1] // s
+    pos = np.array([(0, i, j) for i in range(lh - P + 1) for j in range(lw - P + 1)], np.int32)
+    ctx = Z.Context(0)
+    d = Z.Dictionary(ctx, [torch.from_numpy(mosaic).cuda()], pos, s, P, 0.8)
+    alpha, beta = S.lsh_draws(3, 8, 12, P * P, 4.0)
+    ix = Z.Index(d, 8, 12, 4.0, alpha, beta)
+    wl = G.small_case().wl
+    a = _query(ix, lr, wl, search=1)
+    b = _query(ix, lr, wl, search=2)
+    st = ctx.stats()
+    ctx.sync_status()
+    assert st["n_filter_fallback"] > 0.5 * st["n_queries"], st
+    assert (a["nbr"] == b["nbr"]).all() and (a["dist"] == b["dist"]).all()
+    c = _query(ix, lr, wl, search=3)
+    assert (a["nbr"] == c["nbr"]).all() and (a["dist"] == c["dist"]).all()
