@@ -36,12 +36,21 @@ namespace {
 // issues a 128x128x16 MMA in about 75 cycles (the tensor core executes it in
 // 64), plus about 250 cycles of waits, fence and commit per tile, so one
 // issuing thread per (accumulator buffer, query tile) -- warps 1, 10, 11, 12
-// -- keeps the tensor pipe fed.  Thirteen warps sit 4/3/3/3 on the SM
-// sub-partitions (16K registers each), which caps a thread at 128 registers:
-// the 32-entry lists do not fit, so they keep two issuing warps (1 and 10,
-// one per query tile; 11 warps, 168 registers).
-__host__ __device__ constexpr int tc_mma_warps(int MC) { return MC <= 16 ? 4 : 2; }
-__host__ __device__ constexpr int tc_threads(int MC) { return (9 + tc_mma_warps(MC)) * 32; }
+// -- keeps the tensor pipe fed at K = 80.  Thirteen warps sit 4/3/3/3 on the
+// SM sub-partitions (16K registers each), which caps a thread at 128
+// registers: the 32-entry lists do not fit, so they keep two issuing warps (1
+// and 10, one per query tile; 11 warps, 168 registers).  So do the narrowest
+// operands (K = 32): a tile's MMAs take less time than reading its
+// accumulator, and each round of TMEM loads and their wait costs about 200
+// cycles whatever its width, so their epilogue reads a tile's 128 columns in
+// one round (128 registers) and keeps its chunk list in shared memory (at
+// K = 64 the two issuing threads would cost more than the round saves).
+__host__ __device__ constexpr bool tc_one_round(int KC, int MC) { return KC <= 4 && MC <= 16; }
+__host__ __device__ constexpr int tc_mma_warps(int KC, int MC) {
+  return (MC <= 16 && !tc_one_round(KC, MC)) ? 4 : 2;
+}
+__host__ __device__ constexpr int tc_threads(int KC, int MC) { return (9 + tc_mma_warps(KC, MC)) * 32; }
+__host__ __device__ constexpr int tc_max_regs(int KC, int MC) { return tc_mma_warps(KC, MC) == 4 ? 128 : 168; }
 constexpr int kBarBytes = 512;
 constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
 // Per epilogue lane, chunks below the threshold are first appended to a
@@ -53,16 +62,21 @@ constexpr int TC_ROWS = 128;      // rows per operand tile (M and N of one MMA)
 // take 8, which frees room for a third ring stage.
 __host__ __device__ constexpr int tc_buf(int KC) { return KC >= 20 ? 8 : 16; }
 constexpr int kSmemMax = 232448;  // shared memory a CTA may opt into (227 KB)
+// shared memory of the epilogue: append buffers, and the lists when they
+// live there (value + index per entry and lane)
+__host__ __device__ constexpr int tc_epi_bytes(int KC, int MC) {
+  return tc_buf(KC) * 256 * 8 + (tc_one_round(KC, MC) ? MC * 256 * 8 : 0);
+}
 // Dictionary-tile ring depth: as many bulk copies in flight as the shared
-// memory left by the two query tiles, the barriers and the append buffers
-// holds, up to 16 (KC = 4: 16, 8: 10, 10: 7, 20: 3).
-__host__ __device__ constexpr int tc_stages(int KC) {
-  return (kSmemMax - 1024 - kBarBytes - tc_buf(KC) * 256 * 8 - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16) < 16
-             ? (kSmemMax - 1024 - kBarBytes - tc_buf(KC) * 256 * 8 - 2 * KC * TC_ROWS * 16) /
-                   (KC * TC_ROWS * 16)
+// memory left by the two query tiles, the barriers and the epilogue holds, up
+// to 16 (KC = 4: 16, 8: 10, 10: 7, 20: 3).
+__host__ __device__ constexpr int tc_stages(int KC, int MC) {
+  return (kSmemMax - 1024 - kBarBytes - tc_epi_bytes(KC, MC) - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16) < 16
+             ? (kSmemMax - 1024 - kBarBytes - tc_epi_bytes(KC, MC) - 2 * KC * TC_ROWS * 16) / (KC * TC_ROWS * 16)
              : 16;
 }
-static_assert(tc_stages(4) == 16 && tc_stages(8) == 10 && tc_stages(10) == 7 && tc_stages(20) == 3,
+static_assert(tc_stages(4, 16) == 16 && tc_stages(8, 16) == 10 && tc_stages(8, 32) == 10 &&
+                  tc_stages(10, 16) == 7 && tc_stages(20, 16) == 3,
               "ring depths");
 constexpr uint32_t kWaitNs = 2000000000u;   // 2 s bound on any single wait
 
@@ -359,15 +373,16 @@ __device__ __forceinline__ void chunk_test(float m, int chunk, float thr, float*
 }
 
 template <int KC, int MC, uint32_t AB_TYPE>
-__global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a) {
-  constexpr int kMma = tc_mma_warps(MC);
+__global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
+  constexpr int kMma = tc_mma_warps(KC, MC);
+  constexpr bool kOneRound = tc_one_round(KC, MC);
   constexpr uint32_t kTileBytes = KC * TC_ROWS * 16;  // one 128-row operand tile
   constexpr int kKSteps = KC / 2;                     // MMA K = 16 = two 8-element chunks
   constexpr uint32_t kIdesc = instr_desc(AB_TYPE);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;                                  // 2 query tiles
-  constexpr int kStages = tc_stages(KC);
+  constexpr int kStages = tc_stages(KC, MC);
   unsigned char* sB = smem + 2 * kTileBytes;                 // kStages dictionary tiles
   uint64_t* bars = (uint64_t*)(sB + kStages * kTileBytes);
   uint64_t* a_full = bars + 0;
@@ -383,6 +398,8 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
   constexpr int kBuf = tc_buf(KC);
   float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBuf][256]
   int* buf_i = (int*)(buf_v + kBuf * 256);               // [kBuf][256]
+  float* lst_v = (float*)(buf_i + kBuf * 256);           // [MC][256] lists (one round only)
+  int* lst_i = (int*)(lst_v + MC * 256);                 // [MC][256]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -514,15 +531,41 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
       const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
       const bool valid = q < searched_queries(a);
       const float qn = valid ? a.qn[q] : 0.f;
+      // The sorted chunk list: registers (ld, li), or -- one-round epilogue --
+      // this lane's column of the shared lists, brought into registers only
+      // to merge appended chunks and at the end of the item.
       float ld[MC];
       int li[MC];
+      float* sl_v = lst_v + ew * 32 + lane;
+      int* sl_i = lst_i + ew * 32 + lane;
 #pragma unroll
       for (int j = 0; j < MC; ++j) {
         ld[j] = FLT_MAX;
         li[j] = -1;
+        if constexpr (kOneRound) {
+          sl_v[j * 256] = FLT_MAX;
+          sl_i[j * 256] = -1;
+        }
       }
       float thr = FLT_MAX;   // in acc units: d~ - ||q||^2
       int cnt = 0;           // entries in this lane's append buffer
+      auto flush = [&]() {
+        if constexpr (kOneRound) {
+#pragma unroll
+          for (int j = 0; j < MC; ++j) {
+            ld[j] = sl_v[j * 256];
+            li[j] = sl_i[j * 256];
+          }
+        }
+        flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+        if constexpr (kOneRound) {
+#pragma unroll
+          for (int j = 0; j < MC; ++j) {
+            sl_v[j * 256] = ld[j];
+            sl_i[j * 256] = li[j];
+          }
+        }
+      };
       bool ok = true;
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
@@ -537,29 +580,48 @@ __global__ void __maxnreg__(tc_mma_warps(MC) == 4 ? 128 : 168) k_knn_tc(TcArgs a
         if (++stage == kStages) stage = 0;
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256 + qt * 128);
         // only the chunk minima are used (the loaded values are dead)
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          float va[32], vb[32], ma, mb;
-          tmem_ld32_min_issue(tb + h * 64, va, ma);
-          tmem_ld32_min_issue(tb + h * 64 + 32, vb, mb);
+        if constexpr (kOneRound) {
+          // the tile's four chunks in one round of loads and one wait
+          float va[32], vb[32], vc[32], vd[32], ma, mb, mc, md;
+          tmem_ld32_min_issue(tb, va, ma);
+          tmem_ld32_min_issue(tb + 32, vb, mb);
+          tmem_ld32_min_issue(tb + 64, vc, mc);
+          tmem_ld32_min_issue(tb + 96, vd, md);
           tmem_ld_wait(va, ma);
           tmem_regs_ready(vb, mb);
-          if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
-            tc_fence_before();
-            mbar_arrive(acc_empty + buf * 2 + qt);
+          tmem_regs_ready(vc, mc);
+          tmem_regs_ready(vd, md);
+          tc_fence_before();
+          mbar_arrive(acc_empty + buf * 2 + qt);   // every TMEM read of this tile is done
+          chunk_test(ma, t * 4, thr, bv, bi, cnt);
+          chunk_test(mb, t * 4 + 1, thr, bv, bi, cnt);
+          chunk_test(mc, t * 4 + 2, thr, bv, bi, cnt);
+          chunk_test(md, t * 4 + 3, thr, bv, bi, cnt);
+        } else {
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            float va[32], vb[32], ma, mb;
+            tmem_ld32_min_issue(tb + h * 64, va, ma);
+            tmem_ld32_min_issue(tb + h * 64 + 32, vb, mb);
+            tmem_ld_wait(va, ma);
+            tmem_regs_ready(vb, mb);
+            if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
+              tc_fence_before();
+              mbar_arrive(acc_empty + buf * 2 + qt);
+            }
+            chunk_test(ma, t * 4 + 2 * h, thr, bv, bi, cnt);
+            chunk_test(mb, t * 4 + 2 * h + 1, thr, bv, bi, cnt);
           }
-          chunk_test(ma, t * 4 + 2 * h, thr, bv, bi, cnt);
-          chunk_test(mb, t * 4 + 2 * h + 1, thr, bv, bi, cnt);
         }
         accp[buf] ^= 1u;
         buf ^= 1;
         // room for the next tile's up to 4 appends in every lane; merging
         // here, with the accumulator already handed back, keeps the merge off
         // the MMA's path
-        if (__any_sync(kFull, cnt > kBuf - 4)) flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+        if (__any_sync(kFull, cnt > kBuf - 4)) flush();
       }
       if (!ok) break;
-      flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+      flush();
       if (valid) {
         float* od = a.out_d + ((int64_t)split * a.nq + q) * MC;
         int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
@@ -1118,9 +1180,9 @@ cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_
   return cudaGetLastError();
 }
 
-size_t tc_smem_bytes(int KC) {
-  // alignment pad + operand tiles + barriers + the epilogue append buffers
-  return 1024 + (size_t)(2 + tc_stages(KC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)tc_buf(KC) * 256 * 8;
+size_t tc_smem_bytes(int KC, int MC) {
+  // alignment pad + operand tiles + barriers + the epilogue's buffers (and lists)
+  return 1024 + (size_t)(2 + tc_stages(KC, MC)) * KC * TC_ROWS * 16 + kBarBytes + (size_t)tc_epi_bytes(KC, MC);
 }
 
 int tc_list_size(int precision, int K, int rerank_mult) {
@@ -1133,7 +1195,13 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
   auto kern = k_knn_tc<KC, MC, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, tc_threads(MC), smem, st>>>(args);
+  // the block's warps must fit the register file as compiled (an SM
+  // sub-partition holds 16K registers and takes every fourth warp)
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (fa.maxThreadsPerBlock < tc_threads(KC, MC)) return cudaErrorLaunchOutOfResources;
+  kern<<<grid, tc_threads(KC, MC), smem, st>>>(args);
   return cudaGetLastError();
 }
 
@@ -1159,7 +1227,7 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
   a.tail_split = tail_split;
   if (tail_split > 0 && nsplit != tail_split) return cudaErrorInvalidValue;
   if (MC != 16 && MC != 32) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(kc);
+  const size_t smem = tc_smem_bytes(kc, MC);
   const int items = tail_split > 0 ? a.nq_pairs : a.nsplit * a.nq_pairs;
   grid = grid < items ? grid : items;
   a.full_rounds = tail_split > 0 ? a.nq_pairs / grid : 0;

@@ -150,7 +150,7 @@ cudaError_t launch_operand(const float* feat, int dpad, int d, int64_t n, int64_
 // (precision 0) 10 (K = 80, d <= 25) or 20 (K = 160, d = 50); BF16
 // (precision 1) and single-term FP16 (precision 2) 4 or 8
 int tc_kc(int d, int precision);
-size_t tc_smem_bytes(int KC);
+size_t tc_smem_bytes(int KC, int MC);
 int tc_list_size(int precision, int K, int rerank_mult);
 // tail_split > 0: whole query pairs round robin for the full rounds over the
 // grid, the remaining pairs cut into tail_split dictionary parts (nsplit must
