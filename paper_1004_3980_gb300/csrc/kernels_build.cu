@@ -104,24 +104,37 @@ template <int D>
 __global__ void k_hash(const float* __restrict__ feat, int dpad, int64_t n,
                        const float* __restrict__ alpha, const float* __restrict__ beta, int L, int k,
                        float w, uint64_t* __restrict__ keys) {
-  extern __shared__ float s_ab[];
+  // projections staged with rows padded to DP floats (16-byte loads; the
+  // multiply-adds keep the order of the feature's values)
+  constexpr int DP = (D + 3) / 4 * 4;
+  extern __shared__ float4 s_ab4[];
+  float* s_ab = reinterpret_cast<float*>(s_ab4);
   int nproj = L * k;
-  for (int t = threadIdx.x; t < nproj * D; t += blockDim.x) s_ab[t] = alpha[t];
-  for (int t = threadIdx.x; t < nproj; t += blockDim.x) s_ab[nproj * D + t] = beta[t];
+  for (int t = threadIdx.x; t < nproj * DP; t += blockDim.x) {
+    const int pj = t / DP, q = t % DP;
+    s_ab[t] = q < D ? alpha[pj * D + q] : 0.f;
+  }
+  for (int t = threadIdx.x; t < nproj; t += blockDim.x) s_ab[nproj * DP + t] = beta[t];
   __syncthreads();
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  float v[D];
+  float v[DP];
 #pragma unroll
-  for (int q = 0; q < D; ++q) v[q] = feat[r * dpad + q];
-  const float* s_beta = s_ab + nproj * D;
+  for (int q = 0; q < DP; ++q) v[q] = q < D ? feat[r * dpad + q] : 0.f;
+  const float* s_beta = s_ab + nproj * DP;
   for (int l = 0; l < L; ++l) {
     uint64_t x = (uint64_t)l;
     for (int j = 0; j < k; ++j) {
-      const float* a = s_ab + (l * k + j) * D;
+      const float4* a4 = s_ab4 + (l * k + j) * (DP / 4);
       float acc = 0.f;
 #pragma unroll
-      for (int q = 0; q < D; ++q) acc = fmaf(a[q], v[q], acc);
+      for (int q4 = 0; q4 < DP / 4; ++q4) {
+        const float4 av = a4[q4];
+        acc = fmaf(av.x, v[4 * q4], acc);
+        if (4 * q4 + 1 < D) acc = fmaf(av.y, v[4 * q4 + 1], acc);
+        if (4 * q4 + 2 < D) acc = fmaf(av.z, v[4 * q4 + 2], acc);
+        if (4 * q4 + 3 < D) acc = fmaf(av.w, v[4 * q4 + 3], acc);
+      }
       float t = acc + s_beta[l * k + j];
       int h = (int)floorf(__fdiv_rn(t, w));
       x = zoom_fold_step(x, h, j);
@@ -364,7 +377,7 @@ cudaError_t launch_dict_gather(const float* const* d_lr_images, const int32_t* d
 cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const float* alpha,
                         const float* beta, int L, int k, float w, uint64_t* keys, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  size_t smem = (size_t)L * k * (d + 1) * sizeof(float);
+  size_t smem = (size_t)L * k * ((d + 3) / 4 * 4 + 1) * sizeof(float);
   int blocks = (int)((n + 127) / 128);
 #define ZOOM_HASH(DD)                                                                       \
   do {                                                                                      \

@@ -129,12 +129,12 @@ cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* 
 
 cudaError_t launch_knn_capped(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
                               int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
-                              unsigned long long* counters, cudaStream_t st) {
+                              unsigned long long* fb_count, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  if (ix->dict->d == 9) return capped_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
+  if (ix->dict->d == 9) return capped_dispatch_k<9>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, fb_count, st);
   if (ix->dict->d == 25)
-    return capped_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
-  return launch_knn_capped_grad(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
+    return capped_dispatch_k<25>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, fb_count, st);
+  return launch_knn_capped_grad(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, fb_count, st);
 }
 
 cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,

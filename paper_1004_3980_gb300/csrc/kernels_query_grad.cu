@@ -16,11 +16,11 @@ cudaError_t launch_knn_exact_grad(zoom_index ix, const float* qfeat, const uint6
 
 cudaError_t launch_knn_capped_grad(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
                                    int K, int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
-                                   unsigned long long* counters, cudaStream_t st) {
+                                   unsigned long long* fb_count, cudaStream_t st) {
   if (ix->dict->d == 18)
-    return capped_dispatch_k<18>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
+    return capped_dispatch_k<18>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, fb_count, st);
   if (ix->dict->d == 50)
-    return capped_dispatch_k<50>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, counters, st);
+    return capped_dispatch_k<50>(ix, qfeat, qkeys, nq, K, nbr, dist, cand, fb, fb_count, st);
   return cudaErrorInvalidValue;
 }
 

@@ -900,7 +900,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
     const uint64_t* __restrict__ dkeys, int64_t nd, int L, int tmin, const float* __restrict__ lm,
     const int32_t* __restrict__ lc, int nsplit, int K, int exact, float c_qr, float c_sq, float c_abs,
     int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ fb_list,
-    unsigned long long* __restrict__ counters, int fb_slot, const int32_t* __restrict__ qmap,
+    unsigned long long* __restrict__ fb_count, const int32_t* __restrict__ qmap,
     const unsigned long long* __restrict__ nq_dev) {
   constexpr int kDP = (D + 3) / 4 * 4;   // feature row stride (floats)
   constexpr int kRow4 = kDP / 4;         // 16-byte pieces per row
@@ -1102,7 +1102,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
   const bool flagged = members < K || (exact && !(T - delta > dK));
   if (flagged) {
     if (lane == 0) {
-      const unsigned long long slot = atomicAdd(&counters[fb_slot], 1ull);
+      const unsigned long long slot = atomicAdd(fb_count, 1ull);
       fb_list[slot] = (int32_t)oq;
     }
     return;
@@ -1115,18 +1115,17 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
 
 // Compacts the queries listed in idx[0 .. min(*count, cap)) -- their
 // features and bucket keys -- for a second search; listed queries at or past
-// cap go to the list `over` (count at counters[over_slot]).  One thread per
-// listed query.
+// cap go to the list `over` (count *over_count).  One thread per listed query.
 __global__ void k_gather_queries(const int32_t* __restrict__ idx, const unsigned long long* __restrict__ count,
                                  int64_t cap, const float* __restrict__ feat, int dpad,
                                  const uint64_t* __restrict__ keys, int L, float* __restrict__ cfeat,
                                  uint64_t* __restrict__ ckeys, int32_t* __restrict__ over,
-                                 unsigned long long* __restrict__ counters, int over_slot) {
+                                 unsigned long long* __restrict__ over_count) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= (int64_t)*count) return;
   const int64_t q = idx[j];
   if (j >= cap) {
-    const unsigned long long slot = atomicAdd(&counters[over_slot], 1ull);
+    const unsigned long long slot = atomicAdd(over_count, 1ull);
     over[slot] = (int32_t)q;
     return;
   }
@@ -1248,21 +1247,21 @@ static cudaError_t rerank_k(int K, const float* qfeat, int dpad, const float* qn
                             int64_t nq, const float* dfeat, const uint64_t* dkeys, int64_t nd, int L,
                             int tmin, const float* ld, const int32_t* li, int nsplit, int exact, float c_qr,
                             float c_sq, float c_abs, int32_t* nbr, float* dist, int32_t* fb,
-                            unsigned long long* counters, int fb_slot, const int32_t* qmap,
+                            unsigned long long* fb_count, const int32_t* qmap,
                             const unsigned long long* nq_dev, cudaStream_t st) {
   constexpr int kRerankWarps = rerank_warps(D);
   const int64_t blocks = (nq + kRerankWarps - 1) / kRerankWarps;   // one warp per query
   k_rerank<D, MC><<<(unsigned)blocks, kRerankWarps * 32, 0, st>>>(qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld,
                                                     li, nsplit, K, exact, c_qr, c_sq, c_abs, nbr, dist, fb,
-                                                    counters, fb_slot, qmap, nq_dev);
+                                                    fb_count, qmap, nq_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
-                          cudaStream_t st, int fb_slot, const int32_t* qmap, const unsigned long long* nq_dev) {
+                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* fb_count,
+                          cudaStream_t st, const int32_t* qmap, const unsigned long long* nq_dev) {
   if (nsplit > 8 || K < 1 || K > 16 || dpad != (d + 3) / 4 * 4 || form < 0 || form > 2)
     return cudaErrorInvalidValue;
   if (nq == 0) return cudaSuccess;
@@ -1289,7 +1288,7 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
   const int exact = form != 0;
 #define ZOOM_RR(DD, MM)                                                                          \
   return rerank_k<DD, MM>(K, qfeat, dpad, qn, qkeys, nq, dfeat, dkeys, nd, L, tmin, ld, li, nsplit, \
-                          exact, c_qr, c_sq, c_abs, nbr, dist, fb, counters, fb_slot, qmap, nq_dev, st)
+                          exact, c_qr, c_sq, c_abs, nbr, dist, fb, fb_count, qmap, nq_dev, st)
   if (d == 25 && MC == 16) ZOOM_RR(25, 16);
   if (d == 25 && MC == 32) ZOOM_RR(25, 32);
   if (d == 9 && MC == 16) ZOOM_RR(9, 16);
@@ -1304,11 +1303,11 @@ cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, co
 
 cudaError_t launch_gather_queries(const int32_t* idx, const unsigned long long* count, int64_t max_count,
                                   int64_t cap, const float* feat, int dpad, const uint64_t* keys, int L,
-                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* counters,
-                                  int over_slot, cudaStream_t st) {
+                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* over_count,
+                                  cudaStream_t st) {
   if (max_count == 0) return cudaSuccess;
   if (dpad % 4) return cudaErrorInvalidValue;
   k_gather_queries<<<(unsigned)((max_count + 127) / 128), 128, 0, st>>>(idx, count, cap, feat, dpad, keys, L,
-                                                                         cfeat, ckeys, over, counters, over_slot);
+                                                                         cfeat, ckeys, over, over_count);
   return cudaGetLastError();
 }

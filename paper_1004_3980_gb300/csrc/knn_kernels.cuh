@@ -155,7 +155,7 @@ __global__ __launch_bounds__(128) void k_knn_capped(
     const float* __restrict__ dfeat, int64_t N, int L, const uint64_t* __restrict__ ukeys,
     const int32_t* __restrict__ offs, const int32_t* __restrict__ ids, const int32_t* __restrict__ nuniq,
     int cap, int K, int32_t* __restrict__ nbr, float* __restrict__ dist, int32_t* __restrict__ cand,
-    int32_t* __restrict__ fb_list, unsigned long long* __restrict__ counters) {
+    int32_t* __restrict__ fb_list, unsigned long long* __restrict__ fb_count) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   int32_t* cs = cand + q * cap;
@@ -181,7 +181,7 @@ __global__ __launch_bounds__(128) void k_knn_capped(
     }
   }
   if (nc < K) {
-    const unsigned long long slot = atomicAdd(&counters[CNT_FALLBACK], 1ull);
+    const unsigned long long slot = atomicAdd(fb_count, 1ull);
     fb_list[slot] = (int32_t)q;
     return;
   }
@@ -379,17 +379,17 @@ cudaError_t knn_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qk
 template <int D>
 cudaError_t capped_dispatch_k(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
                               int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
-                              unsigned long long* counters, cudaStream_t st) {
+                              unsigned long long* fb_count, cudaStream_t st) {
   zoom_dict d = ix->dict;
   const int blocks = (int)((nq + 127) / 128);
   if (K <= 8)
     k_knn_capped<D, 8><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n, ix->L, ix->ukeys,
                                                ix->offs, ix->ids, ix->nuniq, ix->cap, K, nbr, dist, cand,
-                                               fb, counters);
+                                               fb, fb_count);
   else
     k_knn_capped<D, 16><<<blocks, 128, 0, st>>>(qfeat, d->dpad, nq, qkeys, d->feat, d->n, ix->L, ix->ukeys,
                                                 ix->offs, ix->ids, ix->nuniq, ix->cap, K, nbr, dist, cand,
-                                                fb, counters);
+                                                fb, fb_count);
   return cudaGetLastError();
 }
 

@@ -370,7 +370,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     return fail(ZOOM_ERR_INVALID_ARG, "min_table_hits must be in 1..L");
   if (lsh->max_candidates < 0 || lsh->max_candidates > 4096)
     return fail(ZOOM_ERR_INVALID_ARG, "max_candidates must be in 0..4096");
-  const size_t smem = (size_t)lsh->L * lsh->k * (d->d + 1) * 4;
+  const size_t smem = (size_t)lsh->L * lsh->k * ((d->d + 3) / 4 * 4 + 1) * 4;
   if (smem > 200 * 1024) return fail(ZOOM_ERR_INVALID_ARG, "L*k*(d+1) too large");
   zoom_ctx ctx = d->ctx;
   cudaStream_t st = (cudaStream_t)stream;
@@ -504,6 +504,7 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   if (ix->cap > 0) {
     p.capped = true;
     Carver c(nullptr);
+    c.take<unsigned long long>(2);
     c.take<int32_t>((size_t)nq * ix->cap);
     c.take<int32_t>(nq);
     p.bytes = c.off + 256;
@@ -569,6 +570,7 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
     p.nsplit2 = (int)std::min<int64_t>(8, nd_tiles);
   }
   Carver c(nullptr);
+  c.take<unsigned long long>(2);
   c.take<uint16_t>(p.q_rows * p.KCH);
   c.take<float>(nq);
   c.take<float>((size_t)p.nsplit * nq * p.MC);
@@ -587,45 +589,57 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   return p;
 }
 
+// Adds a search's fallback counts to the context's statistics.
+__global__ void k_add_fallback_counts(const unsigned long long* __restrict__ cnt,
+                                      unsigned long long* __restrict__ counters) {
+  counters[CNT_FALLBACK] += cnt[0];
+  counters[CNT_FALLBACK2] += cnt[1];
+}
+
 // Neighbour search with a caller-provided workspace of plan.bytes: SIMT
-// scan, or the tensor-core filter + exact rerank (+ SIMT re-run of the
-// queries the rerank could not settle).  Allocates nothing.
+// scan, or the capped walk, or the tensor-core search in its stages (the
+// queries a stage leaves go to the next one, the lists counted in the
+// workspace's own two counters, zeroed here: the workspace may serve many
+// searches of one call or of a recorded batch).  Allocates nothing.
 cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const QueryBufs& b, int64_t nq,
                           const SearchPlan& pl, void* ws, cudaStream_t st) {
   zoom_dict d = ix->dict;
   zoom_ctx ctx = d->ctx;
   const int K = prm->K;
-  if (pl.capped) {
-    Carver s1(ws);
-    int32_t* cand = s1.take<int32_t>((size_t)nq * ix->cap);
-    int32_t* fb = s1.take<int32_t>(nq);
-    cudaError_t e = launch_knn_capped(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, cand, fb, ctx->d_counters, st);
-    if (e == cudaSuccess)
-      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb,
-                           ctx->d_counters + CNT_FALLBACK, st);
-    return e;
-  }
-  if (!pl.tc)
+  if (!pl.tc && !pl.capped)
     return launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, nullptr,
                             nullptr, st);
   Carver s2(ws);
+  unsigned long long* cnt = s2.take<unsigned long long>(2);   // [0] first list, [1] second
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (pl.capped) {
+    int32_t* cand = s2.take<int32_t>((size_t)nq * ix->cap);
+    int32_t* fb = s2.take<int32_t>(nq);
+    e = launch_knn_capped(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, cand, fb, cnt, st);
+    if (e == cudaSuccess)
+      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb, cnt, st);
+    if (e == cudaSuccess) {
+      k_add_fallback_counts<<<1, 1, 0, st>>>(cnt, ctx->d_counters);
+      e = cudaGetLastError();
+    }
+    return e;
+  }
   uint16_t* qop = s2.take<uint16_t>(pl.q_rows * pl.KCH);
   float* qn = s2.take<float>(nq);
   float* ld = s2.take<float>((size_t)pl.nsplit * nq * pl.MC);
   int32_t* li = s2.take<int32_t>((size_t)pl.nsplit * nq * pl.MC);
   int32_t* fb = s2.take<int32_t>(nq);
-  cudaError_t e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
+  e = launch_operand(b.feat, d->dpad, d->d, nq, pl.q_rows, 0, pl.prec, qop, qn, st);
   zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
     e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : pl.prec == 1 ? ix->dopbf : ix->dopf1, d->n, pl.prec,
-                      pl.KCH / 8, pl.MC,
-                      pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
+                      pl.KCH / 8, pl.MC, pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
                       ix->t, ld, li, pl.nsplit, pl.prec == 0 ? 1 : (pl.prec == 1 ? 0 : 2), b.nbr, b.dist, fb,
-                      ctx->d_counters, st);
-  const unsigned long long* n_fb = ctx->d_counters + CNT_FALLBACK;
+                      cnt, st);
   if (pl.prec == 2) {
     // second stage, on the device's count of unsettled queries: compact
     // them, FP16-split operands, the split filter over nsplit2 parts, its
@@ -639,24 +653,24 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
     int32_t* li2 = s2.take<int32_t>((size_t)pl.nsplit2 * pl.cap2 * pl.MC2);
     int32_t* fb2 = s2.take<int32_t>(nq);
     if (e == cudaSuccess)
-      e = launch_gather_queries(fb, n_fb, nq, pl.cap2, b.feat, d->dpad, b.keys, ix->L, cfeat, ckeys, fb2,
-                                ctx->d_counters, CNT_FALLBACK2, st);
+      e = launch_gather_queries(fb, cnt, nq, pl.cap2, b.feat, d->dpad, b.keys, ix->L, cfeat, ckeys, fb2, cnt + 1, st);
     if (e == cudaSuccess)
-      e = launch_operand(cfeat, d->dpad, d->d, pl.cap2, pl.q_rows2, 0, 0, cqop, cqn, st, n_fb);
+      e = launch_operand(cfeat, d->dpad, d->d, pl.cap2, pl.q_rows2, 0, 0, cqop, cqn, st, cnt);
     if (e == cudaSuccess)
       e = launch_knn_tc(cqop, cqn, pl.cap2, ix->dop16, d->n, 0, tc_kc(d->d, 0), pl.MC2, pl.nsplit2, 0, ctx->n_sm,
-                        ld2, li2, ctx->d_status, st, n_fb);
+                        ld2, li2, ctx->d_status, st, cnt);
     if (e == cudaSuccess)
       e = launch_rerank(d->d, pl.MC2, K, cfeat, d->dpad, cqn, ckeys, pl.cap2, d->feat, ix->dkeys, d->n, ix->L,
-                        ix->t, ld2, li2, pl.nsplit2, 1, b.nbr, b.dist, fb2, ctx->d_counters, st, CNT_FALLBACK2, fb,
-                        n_fb);
+                        ix->t, ld2, li2, pl.nsplit2, 1, b.nbr, b.dist, fb2, cnt + 1, st, fb, cnt);
     if (e == cudaSuccess)
-      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb2,
-                           ctx->d_counters + CNT_FALLBACK2, st);
-    return e;
+      e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb2, cnt + 1, st);
+  } else if (e == cudaSuccess) {
+    e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb, cnt, st);
   }
-  if (e == cudaSuccess)
-    e = launch_knn_exact(ix, b.feat, b.keys, nq, K, b.nbr, b.dist, ctx->d_counters, fb, n_fb, st);
+  if (e == cudaSuccess) {
+    k_add_fallback_counts<<<1, 1, 0, st>>>(cnt, ctx->d_counters);
+    e = cudaGetLastError();
+  }
   return e;
 }
 

@@ -18,8 +18,8 @@ enum CounterSlot {
   CNT_PADDED = 3,       // queries with fewer than K candidates
   CNT_FP64 = 4,         // LLE solves in FP64
   CNT_EXACT = 5,        // exact-match (one-hot) queries
-  CNT_FALLBACK = 6,     // tensor-filter queries re-run exactly
-  CNT_FALLBACK2 = 7,    // queries the second (FP16-split) filter left to the SIMT scan
+  CNT_FALLBACK = 6,     // statistics: queries the first tensor filter's rerank did not settle
+  CNT_FALLBACK2 = 7,    // statistics: queries the second (FP16-split) filter left to the SIMT scan
   CNT_N = 8
 };
 
@@ -122,10 +122,10 @@ cudaError_t launch_knn_exact(zoom_index ix, const float* qfeat, const uint64_t* 
                              const int32_t* qidx, const unsigned long long* qcount,
                              cudaStream_t st);
 // capped candidate walk (index cap > 0): cand = scratch [nq][cap]; queries
-// with fewer than K candidates are appended to fb (count in counters)
+// with fewer than K candidates are appended to fb (count *fb_count)
 cudaError_t launch_knn_capped(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq, int K,
                               int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
-                              unsigned long long* counters, cudaStream_t st);
+                              unsigned long long* fb_count, cudaStream_t st);
 cudaError_t launch_lle(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
                        const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
                        unsigned long long* counters, cudaStream_t st);
@@ -135,7 +135,7 @@ cudaError_t launch_knn_exact_grad(zoom_index ix, const float* qfeat, const uint6
                                   const int32_t* qidx, const unsigned long long* qcount, cudaStream_t st);
 cudaError_t launch_knn_capped_grad(zoom_index ix, const float* qfeat, const uint64_t* qkeys, int64_t nq,
                                    int K, int32_t* nbr, float* dist, int32_t* cand, int32_t* fb,
-                                   unsigned long long* counters, cudaStream_t st);
+                                   unsigned long long* fb_count, cudaStream_t st);
 cudaError_t launch_lle_grad(zoom_dict d, const float* qfeat, int64_t nq, const int32_t* nbr,
                             const float* dist, int K, float reg_rel, double cond_thr, float* wgt,
                             unsigned long long* counters, cudaStream_t st);
@@ -162,21 +162,21 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
 // ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
 // chunk index), ascending; form 1 for the FP16-split filter, 2 for the
 // single-term FP16 filter (both: proof and fallback flags), 0 for the BF16
-// filter.  Queries it cannot settle are appended to fb (count at
-// counters[fb_slot]); with qmap, query q of this launch is query qmap[q] of
-// the call (outputs and fb use the latter) and only q < *nq_dev run.
+// filter.  Queries it cannot settle are appended to fb (count *fb_count,
+// zeroed by the caller); with qmap, query q of this launch is query qmap[q]
+// of the call (outputs and fb use the latter) and only q < *nq_dev run.
 cudaError_t launch_rerank(int d, int MC, int K, const float* qfeat, int dpad, const float* qn,
                           const uint64_t* qkeys, int64_t nq, const float* dfeat, const uint64_t* dkeys,
                           int64_t nd, int L, int tmin, const float* ld, const int32_t* li, int nsplit,
-                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* counters,
-                          cudaStream_t st, int fb_slot = CNT_FALLBACK, const int32_t* qmap = nullptr,
+                          int form, int32_t* nbr, float* dist, int32_t* fb, unsigned long long* fb_count,
+                          cudaStream_t st, const int32_t* qmap = nullptr,
                           const unsigned long long* nq_dev = nullptr);
 // The queries idx[0 .. *count) (count <= max_count), compacted: features and
 // keys of the first cap into cfeat / ckeys, the rest appended to `over`.
 cudaError_t launch_gather_queries(const int32_t* idx, const unsigned long long* count, int64_t max_count,
                                   int64_t cap, const float* feat, int dpad, const uint64_t* keys, int L,
-                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* counters,
-                                  int over_slot, cudaStream_t st);
+                                  float* cfeat, uint64_t* ckeys, int32_t* over, unsigned long long* over_count,
+                                  cudaStream_t st);
 
 // backward / adjoint steps (kernels_backward.cu) and the key sort (kernels_build.cu)
 cudaError_t sort_keys_csr(const int32_t* keys32, int64_t n, int32_t* sorted_pos, uint64_t* ukeys,

@@ -140,3 +140,14 @@ def test_later_stages_settle_what_the_single_term_filter_cannot(sigma):
     assert (a["nbr"] == b["nbr"]).all() and (a["dist"] == b["dist"]).all()
     c = _query(ix, lr, wl, search=3)
     assert (a["nbr"] == c["nbr"]).all() and (a["dist"] == c["dist"]).all()
+    # the batched form (autotuning runs the search repeatedly on one
+    # workspace, and a batch runs one search per group): every later stage
+    # must see only its own search's unsettled queries
+    p = G.params(wl, search=2)
+    hr1 = Z.upscale(ix, torch.from_numpy(lr).cuda(), p)
+    lr2 = torch.from_numpy(np.ascontiguousarray(lr[:, ::-1])).cuda()
+    hr2 = Z.upscale(ix, lr2, p)
+    outs, _ = Z.upscale_batch([ix], [torch.from_numpy(lr).cuda(), lr2], p)
+    outs, _ = Z.upscale_batch([ix], [torch.from_numpy(lr).cuda(), lr2], p, outs=outs)
+    Z.batch_release(ctx)
+    assert torch.equal(outs[0], hr1) and torch.equal(outs[1], hr2)
