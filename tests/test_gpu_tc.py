@@ -56,7 +56,7 @@ def test_tc_exact_equals_scan_on_small_workload(small):
     assert st["n_filter_fallback"] < 0.05 * st["n_queries"], st
 
 
-@pytest.mark.parametrize("K", [1, 5, 12])
+@pytest.mark.parametrize("K", [1, 5, 12, 16])
 def test_tc_exact_other_K_and_ragged(small, K):
     case, ctx, d, ix = small
     wl = case.wl
