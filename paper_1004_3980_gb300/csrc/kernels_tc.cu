@@ -12,17 +12,23 @@
 // the entries of the listed chunks in ascending chunk order, tests LSH
 // membership and selects the K nearest members.
 //
-// Exact form (FP16, 3 terms): q = q_hi + q_lo, c = c_hi + c_lo (fp16 pairs),
-//   A row = [q_hi | q_lo | q_hi | 1 | 1 | 0 0 0]            (K = 80)
-//   B row = [-2c_hi | -2c_hi | -2c_lo | n_hi | n_lo | 0 0 0]
-// so acc misses only -2 q_lo.c_lo (about 2^-22 relative).  With an error
-// bound delta on |d~ - d|, a query whose K-th exact distance D_K satisfies
-// T - delta > D_K (T: smallest list threshold over the splits) provably has
-// every nearer member inside the listed chunks; other queries are re-run by
-// the exact SIMT scan.  The result equals the exact scan's.
-// Precision form (BF16, 1 term): A = [q | 1 1 1 | 0..], B = [-2c | n1 n2 n3 | 0..]
-// (K = 32); the rerank examines the listed chunks until a BF16 error bound
-// rules the rest out, without the proof.
+// Three operand forms, one kernel:
+// * single-term FP16 (K = 32, or 64 for 50 features): A = [q | 1 1 1],
+//   B = [-2c | n1 n2 n3] with ||c||^2 as three FP16 terms; q and c rounded to
+//   11 significant bits.  With an error bound delta on |d~ - d|, a query whose
+//   K-th exact distance D_K satisfies T - delta > D_K (T: smallest list
+//   threshold over the splits) provably has every nearer member inside the
+//   listed chunks; the queries it cannot settle are searched again by the
+//   split form (on the device's count of them), and what that leaves by the
+//   exact SIMT scan.  This is the exact search; its result equals the scan's.
+// * FP16 hi/lo split (K = 80, or 160): q = q_hi + q_lo, c = c_hi + c_lo,
+//   A row = [q_hi | q_lo | q_hi | 1 | 1 | 0 0 0],
+//   B row = [-2c_hi | -2c_hi | -2c_lo | n_hi | n_lo | 0 0 0], so acc misses
+//   only -2 q_lo.c_lo (about 2^-22 relative): the same proof with a 30x
+//   smaller bound (the second stage, or alone).
+// * BF16 (K = 32, or 64): A = [q | 1 1 1 | 0..], B = [-2c | n1 n2 n3 | 0..];
+//   the rerank examines the listed chunks until a BF16 error bound rules the
+//   rest out, without the proof (the precision form).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
