@@ -187,9 +187,9 @@ def cpu_oracle_sample(wl: S.Workload, train, pos, alpha, beta, lr, n_sample: int
 def launches_per_step(wl: S.Workload, tc: bool) -> int:
     # features, hash, lookup; the exact tensor search: operand, single-term
     # filter, rerank, then the second stage (gather, split operand, split
-    # filter, rerank) and the SIMT re-run (8), or the SIMT scan (1); LLE,
-    # overlap-add, 2 per back-projection step
-    return 3 + (8 if tc else 1) + 2 + 2 * wl.bp_iters
+    # filter, rerank), the SIMT re-run and the fallback-count update (9), or
+    # the SIMT scan (1); LLE, overlap-add, 2 per back-projection step
+    return 3 + (9 if tc else 1) + 2 + 2 * wl.bp_iters
 
 
 def max_over_ranks(ms: float, world: int, device: str) -> float:
