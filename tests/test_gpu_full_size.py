@@ -1,9 +1,13 @@
 """The 2x zoom of a 512 x 512 LR image with the 1,000,000-pair dictionary
 (5x5 LR / 10x10 HR patches, L = 16, k = 16, K = 8) in the configuration
-bench.py times: the neighbours and distances of 40 sampled queries against
-the oracle (its features, keys, candidate sets and exact K nearest, one
-query at a time), every query's neighbours and distances equal to the SIMT
-scan's, and the search statistics."""
+bench.py times, with the pixel feature (w = 4) and with the first-order
+gradient feature (D = 50, w = 8, as the bench's gradient line): the
+neighbours and distances of 40 sampled queries against the oracle (its
+features, keys, candidate sets and exact K nearest, one query at a time),
+every query's neighbours and distances equal to the SIMT scan's, and the
+search statistics."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -16,35 +20,40 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[(0, None), (1, 8.0)], ids=["pixels", "gradients"])
+def full(request):
     from paper_1004_3980_gb300 import build
     build.build()
     import paper_1004_3980_gb300 as Z
+    F, w = request.param
     wl = S.WORKLOADS["zoom2x_512_dict1m"]
+    if w is not None:
+        wl = dataclasses.replace(wl, w=w)
+    D = O.FEATURE_DIMS[F](wl.patch)
     train = S.training_images(wl)
     lrs = wl.train_hr // wl.scale
     pos = S.sample_positions(wl.pos_seed, len(train), lrs, lrs, wl.patch, wl.n_pairs)
-    alpha, beta = S.lsh_draws(wl.proj_seed, wl.L, wl.k, wl.patch ** 2, wl.w)
+    alpha, beta = S.lsh_draws(wl.proj_seed, wl.L, wl.k, D, wl.w)
     lr = S.test_image(wl)
     ctx = Z.Context(0)
-    d = Z.Dictionary(ctx, [torch.from_numpy(x).cuda() for x in train], pos, wl.scale, wl.patch, wl.blur_sigma)
+    d = Z.Dictionary(ctx, [torch.from_numpy(x).cuda() for x in train], pos, wl.scale, wl.patch, wl.blur_sigma,
+                     feature=F)
     ix = Z.Index(d, wl.L, wl.k, wl.w, alpha, beta)
     # the oracle's dictionary features: the definition of build_dictionary
-    # (the float32 LR training image's patch minus its mean) taken image by
-    # image with patch_features; HR residuals are not needed here
+    # (the feature of the float32 LR training image at each position) taken
+    # image by image with patch_features; HR residuals are not needed here
     P = wl.patch
-    feat = np.empty((len(pos), P * P))
+    feat = np.empty((len(pos), D))
     mu = np.empty(len(pos))
     for m, x in enumerate(train):
         lr_m = O.degrade(np.asarray(x, np.float64), wl.scale, wl.blur_sigma).astype(np.float32)
-        v, mv = O.patch_features(lr_m, P)
+        v, mv = O.patch_features(lr_m, P, F)
         sel = np.flatnonzero(pos[:, 0] == m)
         nw = lr_m.shape[1] - P + 1
         src = pos[sel, 1] * nw + pos[sel, 2]
         feat[sel] = v[src]
         mu[sel] = mv[src]
-    od = O.Dictionary(wl.scale, P, None, feat, mu, None)
+    od = O.Dictionary(wl.scale, P, None, feat, mu, None, F)
     oix = O.build_index(od, alpha, beta, wl.w, wl.L, wl.k)
     return dict(Z=Z, wl=wl, lr=lr, ctx=ctx, d=d, ix=ix, od=od, oix=oix)
 
