@@ -188,8 +188,9 @@ def launches_per_step(wl: S.Workload, tc: bool) -> int:
     # features, hash, lookup; the exact tensor search: operand, single-term
     # filter, rerank, then the second stage (gather, split operand, split
     # filter, rerank), the SIMT re-run and the fallback-count update (9), or
-    # the SIMT scan (1); LLE, overlap-add, 2 per back-projection step
-    return 3 + (9 if tc else 1) + 2 + 2 * wl.bp_iters
+    # the SIMT scan (1); LLE, the two overlap-average passes (blend, average),
+    # 2 per back-projection step
+    return 3 + (9 if tc else 1) + 3 + 2 * wl.bp_iters
 
 
 def max_over_ranks(ms: float, world: int, device: str) -> float:

@@ -39,6 +39,102 @@ __global__ void k_overlap_add(const int32_t* __restrict__ nbr, const float* __re
   hr[(int64_t)Y * W + X] = acc / (float)cnt;
 }
 
+// The same average in two passes, for callers with nq * PH^2 floats of
+// scratch.  Pass 1 blends the patches of 32 consecutive queries of one patch
+// row: the neighbours' residual rows are read whole, in order and 16 bytes
+// per load, each thread blending 4 adjacent patch pixels (the one-pass form
+// reads each 4-byte value from the pixels it covers, scattered over the
+// row), and the blended values leave through shared memory,
+// transposed to the layout [patch row i][patch pixel p][patch column j].
+// Pass 2 averages them per HR pixel: for one covering patch the lanes of a
+// warp then read s runs of consecutive j.  Each blended value is computed
+// with the same operations in the same order as in the one-pass form, and
+// pass 2 sums them in its order, so both forms give the same bits.
+constexpr int kBlendQ = 32;       // queries of one patch row per block
+constexpr int kBlendPC = 128;     // patch pixels per shared-memory round
+constexpr int kBlendMaxK = 64;
+
+__global__ void __launch_bounds__(256) k_blend_rows(const int32_t* __restrict__ nbr,
+                                                    const float* __restrict__ wgt,
+                                                    const float* __restrict__ mu,
+                                                    const float* __restrict__ hr_res, int ph2pad, int K,
+                                                    int nw, int ph2, float* __restrict__ out) {
+  __shared__ int32_t s_nbr[kBlendQ * kBlendMaxK];
+  __shared__ float s_w[kBlendQ * kBlendMaxK];
+  __shared__ float s_mu[kBlendQ];
+  __shared__ float s_t[kBlendPC * (kBlendQ + 1)];
+  const int i = blockIdx.y;
+  const int j0 = blockIdx.x * kBlendQ;
+  const int nqc = min(kBlendQ, nw - j0);
+  const int64_t n0 = (int64_t)i * nw + j0;
+  for (int e = threadIdx.x; e < nqc * K; e += blockDim.x) {
+    s_nbr[e] = nbr[n0 * K + e];
+    s_w[e] = wgt[n0 * K + e];
+  }
+  if ((int)threadIdx.x < nqc) s_mu[threadIdx.x] = mu[n0 + threadIdx.x];
+  __syncthreads();
+  for (int p0 = 0; p0 < ph2; p0 += kBlendPC) {
+    const int pc = min(kBlendPC, ph2 - p0);
+    const int pq = (pc + 3) / 4;   // 4-pixel groups; the last may reach into the row's padding
+    for (int e = threadIdx.x; e < nqc * pq; e += blockDim.x) {
+      const int q = e / pq, pl = 4 * (e - q * pq);
+      const int32_t* nb = s_nbr + q * K;
+      const float* wq = s_w + q * K;
+      const float* col = hr_res + p0 + pl;
+      float4 v = make_float4(s_mu[q], s_mu[q], s_mu[q], s_mu[q]);
+      for (int m0 = 0; m0 < K; m0 += 8) {
+        float4 r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          r[u] = m0 + u < K ? __ldg(reinterpret_cast<const float4*>(col + (int64_t)nb[m0 + u] * ph2pad))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (m0 + u < K) {
+            const float wm = wq[m0 + u];
+            v.x = fmaf(wm, r[u].x, v.x);
+            v.y = fmaf(wm, r[u].y, v.y);
+            v.z = fmaf(wm, r[u].z, v.z);
+            v.w = fmaf(wm, r[u].w, v.w);
+          }
+      }
+      float* t = s_t + pl * (kBlendQ + 1) + q;
+      t[0] = v.x;
+      if (pl + 1 < pc) t[kBlendQ + 1] = v.y;
+      if (pl + 2 < pc) t[2 * (kBlendQ + 1)] = v.z;
+      if (pl + 3 < pc) t[3 * (kBlendQ + 1)] = v.w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < pc * kBlendQ; e += blockDim.x) {
+      const int pl = e / kBlendQ, q = e % kBlendQ;
+      if (q < nqc) out[((int64_t)i * ph2 + p0 + pl) * nw + j0 + q] = s_t[pl * (kBlendQ + 1) + q];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_overlap_average(const float* __restrict__ pb, int h, int w, int s, int P,
+                                  float* __restrict__ hr) {
+  const int W = s * w, H = s * h;
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= W || Y >= H) return;
+  const int PH = s * P, nh = h - P + 1, nw = w - P + 1, ph2 = PH * PH;
+  const int i_hi = min(Y / s, nh - 1), j_hi = min(X / s, nw - 1);
+  const int i_lo = Y >= PH ? (Y - PH) / s + 1 : 0;
+  const int j_lo = X >= PH ? (X - PH) / s + 1 : 0;
+  float acc = 0.f;
+  int cnt = 0;
+  for (int i = i_lo; i <= i_hi; ++i) {
+    const float* row = pb + ((int64_t)i * ph2 + (Y - s * i) * PH) * nw;
+    for (int j = j_lo; j <= j_hi; ++j) {
+      acc += __ldg(row + (int64_t)(X - s * j) * nw + j);
+      ++cnt;
+    }
+  }
+  hr[(int64_t)Y * W + X] = acc / (float)cnt;
+}
+
 // e = D(B x) - y on the LR grid (FP32).  The blur and the box mean combine
 // into separable 1-D weights over the (s+2)-wide window.
 struct Wts1D {
@@ -118,6 +214,21 @@ cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float
                                float* hr, cudaStream_t st) {
   dim3 blk(32, 8), grd((s * w + 31) / 32, (s * h + 7) / 8);
   k_overlap_add<<<grd, blk, 0, st>>>(nbr, wgt, mu, hr_res, ph2pad, K, h, w, s, P, hr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_add_staged(const int32_t* nbr, const float* wgt, const float* mu,
+                                      const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
+                                      float* patches, float* hr, cudaStream_t st) {
+  const int nh = h - P + 1, nw = w - P + 1, PH = s * P;
+  // 16-byte loads of the residual rows: 16-byte aligned rows, padded to 4
+  if (K > kBlendMaxK || nh > 65535 || !patches || ph2pad % 4 != 0 || ph2pad < PH * PH ||
+      reinterpret_cast<uintptr_t>(hr_res) % 16 != 0)
+    return launch_overlap_add(nbr, wgt, mu, hr_res, ph2pad, K, h, w, s, P, hr, st);
+  dim3 g1((nw + kBlendQ - 1) / kBlendQ, nh);
+  k_blend_rows<<<g1, 256, 0, st>>>(nbr, wgt, mu, hr_res, ph2pad, K, nw, PH * PH, patches);
+  dim3 blk(32, 8), g2((s * w + 31) / 32, (s * h + 7) / 8);
+  k_overlap_average<<<g2, blk, 0, st>>>(patches, h, w, s, P, hr);
   return cudaGetLastError();
 }
 

@@ -776,7 +776,11 @@ zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt
   if (K < 1 || K > 64) return fail(ZOOM_ERR_INVALID_ARG, "K must be in 1..64");
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(d->ctx->device));
-  cudaError_t e = launch_overlap_add(nbr, wgt, mu, d->hr_res, d->ph2pad, K, h, w, d->s, d->P, hr, st);
+  Scratch scr(d->ctx, st);
+  if (!scr.get((size_t)(h - d->P + 1) * (w - d->P + 1) * d->ph2 * 4))
+    return fail(ZOOM_ERR_OOM, "reconstruct scratch");
+  cudaError_t e = launch_overlap_add_staged(nbr, wgt, mu, d->hr_res, d->ph2pad, K, h, w, d->s, d->P,
+                                            (float*)scr.p, hr, st);
   if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("reconstruct: ") + cudaGetErrorString(e));
   return ZOOM_OK;
 }
@@ -845,6 +849,7 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   c.take<float>(nq * K);
   c.take<float>((size_t)s * h * s * w);
   c.take<float>((size_t)h * w);
+  c.take<float>(nq * d->ph2);
   Scratch scr(d->ctx, st);
   if (!scr.get(c.off + 256)) return fail(ZOOM_ERR_OOM, "upscale scratch");
   Carver s2(scr.p);
@@ -859,9 +864,11 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   b.bucket_sum = nullptr;
   float* tmp = s2.take<float>((size_t)s * h * s * w);
   float* err = s2.take<float>((size_t)h * w);
+  float* patches = s2.take<float>(nq * d->ph2);
   rc = run_query_steps(ix, lr, h, w, prm, b, st);
   if (rc != ZOOM_OK) return rc;
-  cudaError_t e = launch_overlap_add(b.nbr, b.wgt, b.mu, d->hr_res, d->ph2pad, K, h, w, s, d->P, hr, st);
+  cudaError_t e =
+      launch_overlap_add_staged(b.nbr, b.wgt, b.mu, d->hr_res, d->ph2pad, K, h, w, s, d->P, patches, hr, st);
   if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("overlap-add: ") + cudaGetErrorString(e));
   zoom_stage_mark(d->ctx, 6, st);
   rc = run_backproject(d->ctx, s, d->blur_sigma, lr, h, w, prm, hr, tmp, err, st);
@@ -1137,10 +1144,18 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
       c.take<float>(g.nq * prm->K);
       c.take<char>(0);
     }
+    // one buffer of blended patches, reused image after image
+    int64_t max_patch = 0;
+    for (auto& g : groups)
+      for (int i : g.images) {
+        zoom_dict d = g.ix->dict;
+        max_patch = std::max<int64_t>(max_patch, (int64_t)(h[i] - d->P + 1) * (w[i] - d->P + 1) * d->ph2);
+      }
     for (int i = 0; i < n_images; ++i) {
       c.take<float>((size_t)h[i] * w[i] * scale[i] * scale[i]);
       c.take<float>((size_t)h[i] * w[i]);
     }
+    c.take<float>(max_patch);
     const size_t base_bytes = c.off + 256;
     // the query buffers first (the autotuner needs features and keys)
     rec->bytes = base_bytes;
@@ -1168,6 +1183,7 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
       tmp[i] = m.take<float>((size_t)h[i] * w[i] * scale[i] * scale[i]);
       err[i] = m.take<float>((size_t)h[i] * w[i]);
     }
+    float* patches = m.take<float>(max_patch);
     // features and keys of every image, then one autotuning pass per group
     for (auto& g : groups) {
       zoom_dict d = g.ix->dict;
@@ -1248,8 +1264,8 @@ zoom_status zoom_upscale_batch(const zoom_index* ixs, int32_t n_indexes, int32_t
       for (size_t k = 0; k < g.images.size() && e == cudaSuccess; ++k) {
         const int i = g.images[k];
         const int64_t o = g.q_off[k];
-        e = launch_overlap_add(g.b.nbr + o * prm->K, g.b.wgt + o * prm->K, g.b.mu + o, d->hr_res, d->ph2pad,
-                               prm->K, h[i], w[i], d->s, d->P, hr[i], cs);
+        e = launch_overlap_add_staged(g.b.nbr + o * prm->K, g.b.wgt + o * prm->K, g.b.mu + o, d->hr_res,
+                                      d->ph2pad, prm->K, h[i], w[i], d->s, d->P, patches, hr[i], cs);
         float* a = hr[i];
         float* bb = tmp[i];
         for (int it = 0; it < prm->bp_iters && e == cudaSuccess; ++it) {

@@ -203,6 +203,11 @@ cudaError_t launch_nbr_dist(const float* qfeat, int dpad, int d, int64_t nq, con
 cudaError_t launch_overlap_add(const int32_t* nbr, const float* wgt, const float* mu,
                                const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
                                float* hr, cudaStream_t st);
+// the same average through nq * (s P)^2 floats of scratch (two passes, the
+// same bits; falls back to the one-pass form where the scratch is NULL)
+cudaError_t launch_overlap_add_staged(const int32_t* nbr, const float* wgt, const float* mu,
+                                      const float* hr_res, int ph2pad, int K, int h, int w, int s, int P,
+                                      float* patches, float* hr, cudaStream_t st);
 cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, float* err, int h,
                                 int w, int s, double blur_sigma, float sigma_sp, float sigma_r,
                                 int radius, cudaStream_t st);
