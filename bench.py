@@ -360,6 +360,11 @@ def run_single(a, wl, config, rank, world, local):
         if ms > 0:
             gbs = byts / (ms / 1e3) / 1e9
             kernels[name] = {"ms": ms, "algorithmic_bytes": byts, "GB/s": gbs, "frac_hbm": gbs / hbm_peak}
+    if "overlap_add" in kernels:
+        # blend pass + average pass; DRAM traffic from the committed ncu summary
+        kernels["overlap_add"]["kernels"] = "k_blend_rows + k_overlap_average"
+        kernels["overlap_add"]["traffic"] = profiled_traffic("paper_1004_3980_gb300/csrc/kernels_image.cu",
+                                                             "profiles/overlap_average_zoom2x_512_dict1m.md")
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
