@@ -883,6 +883,22 @@ __device__ __forceinline__ void warp_merge_best(float& bd, int& bi, float v, int
   bi = ai;
 }
 
+// t-of-L membership: at least tmin of the entry's L bucket keys equal the
+// query's.  Eight tables at a time (loads issued together); stops at tmin
+// hits.
+__device__ __forceinline__ bool lsh_member(const uint64_t* __restrict__ dk, const uint64_t* qk, int L,
+                                           int tmin) {
+  int hits = 0;
+  for (int l0 = 0; l0 < L && hits < tmin; l0 += 8) {
+    uint64_t kk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) kk[j] = l0 + j < L ? __ldg(dk + l0 + j) : 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) hits += (l0 + j < L && kk[j] == qk[l0 + j]) ? 1 : 0;
+  }
+  return hits >= tmin;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src)
                : "memory");
@@ -1032,22 +1048,26 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
         }
       }
     }
-    // entries that could still enter the K best: LSH membership (the
-    // entry's keys eight tables at a time, loads issued together; stop at
-    // t hits)
+    // entries that could still enter the K best: LSH membership
+    int eid = dd != FLT_MAX ? (int)e : INT_MAX;
     bool mem = false;
-    if (dd != FLT_MAX && (members < K || dd < dK || (dd == dK && (int)e < iK))) {
-      const uint64_t* dk = dkeys + e * L;
-      const uint64_t* qk = s_qk[wib];
-      int hits = 0;
-      for (int l0 = 0; l0 < L && hits < tmin; l0 += 8) {
-        uint64_t kk[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) kk[j] = l0 + j < L ? __ldg(dk + l0 + j) : 0ull;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) hits += (l0 + j < L && kk[j] == qk[l0 + j]) ? 1 : 0;
+    if (members < K) {
+      // fewer than K members so far (the first chunk): every entry could
+      // enter, so the chunk is sorted by (distance, ID) across the lanes and
+      // membership taken in that order, a few lanes past the members still
+      // needed at a time; once K members are known no later entry can enter
+      warp_sort32(dd, eid, lane);
+      const int need = K - members;
+      int found = 0;
+      for (int j0 = 0; j0 < 32 && found < need;) {
+        const int j1 = min(32, j0 + need - found + 4);
+        if (lane >= j0 && lane < j1 && dd != FLT_MAX)
+          mem = lsh_member(dkeys + (int64_t)eid * L, s_qk[wib], L, tmin);
+        found = __popc(__ballot_sync(kFull, mem));
+        j0 = j1;
       }
-      mem = hits >= tmin;
+    } else if (dd != FLT_MAX && (dd < dK || (dd == dK && eid < iK))) {
+      mem = lsh_member(dkeys + (int64_t)eid * L, s_qk[wib], L, tmin);
     }
     unsigned mm = __ballot_sync(kFull, mem);
     members += __popc(mm);
@@ -1055,7 +1075,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
       // many (the first chunks): sort the chunk's members across the lanes
       // and merge them with the K best
       float v = mem ? dd : FLT_MAX;
-      int id = mem ? (int)e : INT_MAX;
+      int id = mem ? eid : INT_MAX;
       warp_sort32(v, id, lane);
       warp_merge_best(bd, bi, v, id, K, lane);
       mm = 0;
@@ -1064,7 +1084,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
     while (mm) {
       const bool mine = (mm >> lane) & 1u;
       float v = mine ? dd : FLT_MAX;
-      int id = mine ? (int)e : INT_MAX;
+      int id = mine ? eid : INT_MAX;
       int src = lane;
 #pragma unroll
       for (int off = 16; off; off >>= 1) {
