@@ -206,14 +206,15 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature
     added back at reconstruction time.  Position k in ``positions`` (sorted by
     image, row, column) is the unique ID k.  Features 1 and 2: the gradients
     of the whole (float32) LR training image at the patch's pixels."""
-    lr_imgs = [degrade(np.asarray(x, np.float64), s, sigma).astype(np.float32) for x in hr_images]
+    hr64 = [np.asarray(x, np.float64) for x in hr_images]
+    lr_imgs = [degrade(x, s, sigma).astype(np.float32) for x in hr64]
     PH = s * P
     N = len(positions)
     lr_pix = np.empty((N, P * P), np.float32)
     hr = np.empty((N, PH * PH))
     for n, (m, i, j) in enumerate(np.asarray(positions)):
         lr_pix[n] = lr_imgs[m][i:i + P, j:j + P].ravel()
-        hr[n] = np.asarray(hr_images[m], np.float64)[s * i:s * i + PH, s * j:s * j + PH].ravel()
+        hr[n] = hr64[m][s * i:s * i + PH, s * j:s * j + PH].ravel()
     lr64 = lr_pix.astype(np.float64)
     mu = lr64.mean(axis=1)
     if feature == 0:
