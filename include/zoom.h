@@ -297,8 +297,9 @@ zoom_status zoom_query(zoom_index ix, const float* lr, int32_t h, int32_t w,
  * the overlap average (no back-projection).  nbr int32 [n_q][K], wgt float32
  * [n_q][K], mu float32 [n_q] (device); hr device (s*h) x (s*w).  Takes
  * n_q * (s*P)^2 floats of scratch from the context allocator for the blended
- * patches (ZOOM_ERR_OOM if it fails); zoom_reconstruct_with needs none and
- * gives the same bits. */
+ * patches of a two-pass average; where that allocation fails it runs the
+ * one-pass form of zoom_reconstruct_with, which needs none and gives the
+ * same bits. */
 zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt, const float* mu,
                              int32_t h, int32_t w, int32_t K, float* hr, void* stream);
 

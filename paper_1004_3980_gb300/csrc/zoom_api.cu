@@ -776,11 +776,12 @@ zoom_status zoom_reconstruct(zoom_index ix, const int32_t* nbr, const float* wgt
   if (K < 1 || K > 64) return fail(ZOOM_ERR_INVALID_ARG, "K must be in 1..64");
   cudaStream_t st = (cudaStream_t)stream;
   ZCHECK_CUDA(cudaSetDevice(d->ctx->device));
+  // the blended patches of the two-pass form; without room for them the
+  // one-pass form (the same bits)
   Scratch scr(d->ctx, st);
-  if (!scr.get((size_t)(h - d->P + 1) * (w - d->P + 1) * d->ph2 * 4))
-    return fail(ZOOM_ERR_OOM, "reconstruct scratch");
-  cudaError_t e = launch_overlap_add_staged(nbr, wgt, mu, d->hr_res, d->ph2pad, K, h, w, d->s, d->P,
-                                            (float*)scr.p, hr, st);
+  float* patches = scr.get((size_t)(h - d->P + 1) * (w - d->P + 1) * d->ph2 * 4) ? (float*)scr.p : nullptr;
+  cudaError_t e = launch_overlap_add_staged(nbr, wgt, mu, d->hr_res, d->ph2pad, K, h, w, d->s, d->P, patches,
+                                            hr, st);
   if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("reconstruct: ") + cudaGetErrorString(e));
   return ZOOM_OK;
 }
@@ -849,7 +850,6 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   c.take<float>(nq * K);
   c.take<float>((size_t)s * h * s * w);
   c.take<float>((size_t)h * w);
-  c.take<float>(nq * d->ph2);
   Scratch scr(d->ctx, st);
   if (!scr.get(c.off + 256)) return fail(ZOOM_ERR_OOM, "upscale scratch");
   Carver s2(scr.p);
@@ -864,9 +864,12 @@ zoom_status zoom_upscale(zoom_index ix, const float* lr, int32_t h, int32_t w, i
   b.bucket_sum = nullptr;
   float* tmp = s2.take<float>((size_t)s * h * s * w);
   float* err = s2.take<float>((size_t)h * w);
-  float* patches = s2.take<float>(nq * d->ph2);
   rc = run_query_steps(ix, lr, h, w, prm, b, st);
   if (rc != ZOOM_OK) return rc;
+  // the blended patches of the two-pass overlap average; without room for
+  // them the one-pass form (the same bits)
+  Scratch pscr(d->ctx, st);
+  float* patches = pscr.get((size_t)nq * d->ph2 * 4) ? (float*)pscr.p : nullptr;
   cudaError_t e =
       launch_overlap_add_staged(b.nbr, b.wgt, b.mu, d->hr_res, d->ph2pad, K, h, w, s, d->P, patches, hr, st);
   if (e != cudaSuccess) return fail(ZOOM_ERR_CUDA, std::string("overlap-add: ") + cudaGetErrorString(e));
