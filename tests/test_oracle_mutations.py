@@ -8,6 +8,7 @@ import pytest
 from oracle import zoom_oracle as O
 from tests import test_golden as TG
 from tests import test_oracle_degrade as TD
+from tests import test_oracle_dictionary as TDI
 from tests import test_oracle_features as TF
 from tests import test_oracle_hash as TH
 from tests import test_oracle_knn_lle as TK
@@ -156,3 +157,68 @@ def test_horizontal_only_gradient_mass_is_caught(monkeypatch):
     # the sampling mass taken from g_x alone
     monkeypatch.setattr(O, "gradient_magnitude", lambda img: np.abs(O.gradient_images(img)[0]))
     _fails(TS.test_a_single_bright_pixel_splits_the_draws_four_ways)
+
+
+def _bp_variant(range_sq, mean_kernel, guide):
+    """back_project with one planted change in the range term of Eq. 15:
+    range_sq(sigma_r) is the divisor of the squared difference, mean_kernel
+    the window weights of the mean, guide picks the image the term reads."""
+    def bp(x, y, s, blur_sigma, iters, sigma_sp, sigma_r, radius):
+        x = np.asarray(x, np.float64).copy()
+        ck = O.spatial_kernel(sigma_sp, radius)
+        for _ in range(iters):
+            e = O.degrade(x, s, blur_sigma) - y
+            u = np.kron(e, np.ones((s, s)))
+            g = O.window_sum_clamped(u, ck)
+            gd = guide(x, u)
+            m = O.window_sum_clamped(gd, mean_kernel(sigma_sp, radius))
+            x = x - np.exp(-(gd - m) ** 2 / range_sq(sigma_r)) * g
+        return x
+    return bp
+
+
+_BOX = lambda sp, R: np.full((2 * R + 1, 2 * R + 1), 1.0 / (2 * R + 1) ** 2)
+_TWO_SQ = lambda sr: 2.0 * sr * sr
+_GUIDE_X = lambda x, u: x
+
+
+@pytest.mark.parametrize("variant", [
+    _bp_variant(lambda sr: sr * sr, _BOX, _GUIDE_X),                 # sigma_r^2 instead of 2 sigma_r^2
+    _bp_variant(_TWO_SQ, O.spatial_kernel, _GUIDE_X),                # Gaussian-weighted mean, not the box
+    _bp_variant(_TWO_SQ, _BOX, lambda x, u: u),                      # the error image as the guide
+    _bp_variant(_TWO_SQ, lambda sp, R: _BOX(sp, R - 1), _GUIDE_X),  # a 5 x 5 window for the mean
+], ids=["sigma_r_squared", "gaussian_mean", "error_guide", "window_5x5"])
+def test_range_weight_mistakes_are_caught(monkeypatch, variant):
+    # every variant still passes the flat-guide and sigma_r -> infinity pins
+    # that were all the range term had before; the step-edge pin sees each
+    monkeypatch.setattr(O, "back_project", variant)
+    TR.test_bp_flat_guide_has_unit_range_weight()
+    TR.test_bp_without_range_term_is_gaussian_step(np.random.default_rng(0))
+    _fails(TR.test_bp_range_weight_at_a_step_edge, 0.3, 0.5, 0.1)
+
+
+def _dictionary_variant(hr_origin):
+    """build_dictionary (feature 0) with the HR patch cut at hr_origin(s, i, j)."""
+    def build(hr_images, positions, s, P, sigma, feature=0):
+        hr64 = [np.asarray(x, np.float64) for x in hr_images]
+        lr_imgs = [O.degrade(x, s, sigma).astype(np.float32) for x in hr64]
+        PH = s * P
+        lr_pix = np.stack([lr_imgs[m][i:i + P, j:j + P].ravel() for m, i, j in positions])
+        hr = []
+        for m, i, j in positions:
+            Y, X = hr_origin(s, i, j)
+            hr.append(hr64[m][Y:Y + PH, X:X + PH].ravel())
+        mu = lr_pix.astype(np.float64).mean(axis=1)
+        return O.Dictionary(s, P, lr_pix, lr_pix - mu[:, None], mu, np.stack(hr) - mu[:, None], 0)
+    return build
+
+
+@pytest.mark.parametrize("origin", [
+    lambda s, i, j: (s * i + 1, s * j),     # one HR row too low
+    lambda s, i, j: (s * i, s * j + 1),     # one HR column too far right
+    lambda s, i, j: (s * j, s * i),         # row and column swapped
+    lambda s, i, j: (i, j),                 # the LR origin used on the HR image
+], ids=["row_plus_one", "col_plus_one", "swapped", "lr_origin"])
+def test_hr_cut_mistakes_are_caught(monkeypatch, origin):
+    monkeypatch.setattr(O, "build_dictionary", _dictionary_variant(origin))
+    _fails(TDI.test_dictionary_entries_of_a_ramp_have_closed_forms, 2, 5)

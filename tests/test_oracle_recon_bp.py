@@ -188,3 +188,44 @@ def test_prior_brute_force():
                         b = p[i2 * nw + j2, (Y - s * i2) * PH + X - s * j2]
                         tot += (a - b) ** 2
     assert abs(O.overlap_prior(p, h, w, s, P) - tot) < 1e-10
+
+
+def _step_edge(a, b, H=24, W=24, edge=12):
+    x = np.full((H, W), a)
+    x[:, edge:] = b
+    return x
+
+
+def _hand_range_weight(a, b, X, edge, radius, sigma_r):
+    """Range weight of Eq. 15 at column X of a vertical step edge (a left of
+    `edge`, b from it on), worked out by hand: the (2R+1)^2 box mean of the
+    guide counts the window's columns on each side of the edge (rows do not
+    matter), m = (n_a a + n_b b) / (2R+1)."""
+    cols = np.arange(X - radius, X + radius + 1)
+    n_b = int((cols >= edge).sum())
+    n_a = 2 * radius + 1 - n_b
+    m = (n_a * a + n_b * b) / (2 * radius + 1)
+    xv = b if X >= edge else a
+    return np.exp(-(xv - m) ** 2 / (2.0 * sigma_r ** 2))
+
+
+@pytest.mark.parametrize("a,b,sigma_r", [(0.3, 0.5, 0.1), (0.7, 0.55, 0.08)])
+def test_bp_range_weight_at_a_step_edge(a, b, sigma_r):
+    # Eq. 15 with a non-flat guide.  The LR data is the degradation of the
+    # guide minus a constant c, so the error image is c everywhere and its
+    # normalised Gaussian filtering is c: one step is x - r * c, and r must
+    # be exp(-(x - m)^2 / (2 sigma_r^2)) with m the 7 x 7 box mean of the
+    # current HR estimate x, which at a step edge is a known mix of a and b.
+    s, edge, R, c = 2, 12, 3, 0.05
+    x = _step_edge(a, b, edge=edge)
+    y = O.degrade(x, s, 0.8) - c
+    got = O.back_project(x, y, s, 0.8, 1, 1.5, sigma_r, R)
+    r_got = (x - got) / c
+    for X in range(edge - 5, edge + 5):
+        r_hand = _hand_range_weight(a, b, X, edge, R, sigma_r)
+        np.testing.assert_allclose(r_got[:, X], r_hand, rtol=0, atol=1e-12)
+    # next to the edge the weight is well below 1 (so the pin sees the term)
+    assert _hand_range_weight(a, b, edge, edge, R, sigma_r) < 0.9
+    # far from the edge the window is flat: weight 1
+    np.testing.assert_allclose(r_got[:, :edge - 4], 1.0, atol=1e-12)
+    np.testing.assert_allclose(r_got[:, edge + 4:], 1.0, atol=1e-12)
