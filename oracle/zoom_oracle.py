@@ -196,7 +196,8 @@ class Dictionary:
         return self.scale * self.patch
 
 
-def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature: int = 0) -> Dictionary:
+def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature: int = 0,
+                     with_hr: bool = True) -> Dictionary:
     """Training pairs (Sec. 2.1, Sec. 5.1): every HR training image is blurred
     and down-sampled; at each position (image, i, j) the LR patch at (i, j) is
     paired with the HR patch of side s*P at (s*i, s*j).
@@ -205,16 +206,20 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature
     test LR image; the LR patch mean is subtracted from both patches and is
     added back at reconstruction time.  Position k in ``positions`` (sorted by
     image, row, column) is the unique ID k.  Features 1 and 2: the gradients
-    of the whole (float32) LR training image at the patch's pixels."""
+    of the whole (float32) LR training image at the patch's pixels.
+    with_hr=False leaves hr_res out (None): the search needs only the LR side,
+    and an entry's HR residual depends on its own position alone, so a
+    dictionary built from a subset of the positions gives those entries'."""
     hr64 = [np.asarray(x, np.float64) for x in hr_images]
     lr_imgs = [degrade(x, s, sigma).astype(np.float32) for x in hr64]
     PH = s * P
     N = len(positions)
     lr_pix = np.empty((N, P * P), np.float32)
-    hr = np.empty((N, PH * PH))
+    hr = np.empty((N, PH * PH)) if with_hr else None
     for n, (m, i, j) in enumerate(np.asarray(positions)):
         lr_pix[n] = lr_imgs[m][i:i + P, j:j + P].ravel()
-        hr[n] = hr64[m][s * i:s * i + PH, s * j:s * j + PH].ravel()
+        if with_hr:
+            hr[n] = hr64[m][s * i:s * i + PH, s * j:s * j + PH].ravel()
     lr64 = lr_pix.astype(np.float64)
     mu = lr64.mean(axis=1)
     if feature == 0:
@@ -226,7 +231,7 @@ def build_dictionary(hr_images, positions, s: int, P: int, sigma: float, feature
             gx, gy = grads[m]
             feat[n, :P * P] = gx[i:i + P, j:j + P].ravel()
             feat[n, P * P:] = gy[i:i + P, j:j + P].ravel()
-    return Dictionary(s, P, lr_pix, feat, mu, hr - mu[:, None], feature)
+    return Dictionary(s, P, lr_pix, feat, mu, hr - mu[:, None] if with_hr else None, feature)
 
 
 def dictionary_from_lr_hr(lr_img, hr_img, s: int, P: int, feature: int = 0) -> Dictionary:
@@ -354,9 +359,15 @@ class LshIndex:
 
 def build_index(d: Dictionary, alpha, beta, w: float, L: int, k: int) -> LshIndex:
     """Hash every dictionary feature into L tables (Sec. 4.1: the ID of each
-    training patch is stored in the bin of its k hash values, per table)."""
-    h, margin = hash_values(d.feat, alpha, beta, w)
-    keys = fold_keys(h, L, k)
+    training patch is stored in the bin of its k hash values, per table).
+    Entries are hashed in blocks of rows (each row's values depend on that
+    row alone) to bound the memory of the projections."""
+    n = d.feat.shape[0]
+    keys = np.empty((n, L), np.uint64)
+    margin = np.empty(n)
+    for r0 in range(0, n, 1 << 18):
+        h, margin[r0:r0 + (1 << 18)] = hash_values(d.feat[r0:r0 + (1 << 18)], alpha, beta, w)
+        keys[r0:r0 + (1 << 18)] = fold_keys(h, L, k)
     buckets = []
     for l in range(L):
         order = np.argsort(keys[:, l], kind="stable")
