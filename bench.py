@@ -246,7 +246,7 @@ def oracle_block_queries(wl, lr, od, oi, origins, threads: int):
         part = res[b * BLOCK:(b + 1) * BLOCK]
         cat = lambda f: np.concatenate([getattr(q, f) for q, _ in part])
         out.append({"nbr": cat("nbr"), "dist": cat("dist"), "mu": cat("mu"), "margin": cat("margin"),
-                    "n_cand": cat("n_cand"), "wgt": np.concatenate([w for _, w in part])})
+                    "n_cand": cat("n_cand"), "feat": cat("feat"), "wgt": np.concatenate([w for _, w in part])})
     return out, wall
 
 
@@ -264,16 +264,24 @@ def oracle_block_hr(wl, train, pos, blk):
     return O.reconstruct(local, blk["wgt"], blk["mu"], dh, side, side)
 
 
-def excluded(blk, dict_margin, K, rel=1e-6, bnd=1e-5):
-    """Queries left out of the bit-exact neighbour comparison: a projection of
-    the query, or of one of its K+1 nearest, within bnd (units of w) of a bin
-    boundary, or two of its K+1 nearest FP64 distances within rel of each
-    other."""
-    ex = blk["margin"] < bnd
-    ex |= (dict_margin[blk["nbr"]] < bnd).any(axis=1)
-    d = blk["dist"]
-    ex |= (np.diff(d, axis=1) <= rel * np.maximum(d[:, 1:], 1e-30)).any(axis=1)
-    return ex
+def block_exclusions(blocks, od, oi, threads):
+    """Per block, the queries left out of the bit-exact neighbour comparison
+    (the oracle's neighbour_exclusions: a bin boundary of the query or of an
+    entry that could enter its K nearest, or an FP64 near-tie), one query row
+    per task."""
+    from oracle import zoom_oracle as O
+    fn = (od.feat * od.feat).sum(axis=1)
+
+    def task(args):
+        b, r = args
+        sl = slice(r * BLOCK, (r + 1) * BLOCK)
+        blk = blocks[b]
+        return O.neighbour_exclusions(blk["feat"][sl], blk["margin"][sl], blk["dist"][sl], od, oi, feat_norm2=fn)
+
+    jobs = [(b, r) for b in range(len(blocks)) for r in range(BLOCK)]
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        res = list(ex.map(task, jobs))
+    return [np.concatenate(res[b * BLOCK:(b + 1) * BLOCK]) for b in range(len(blocks))]
 
 
 def oracle_bp_seconds_per_px(wl, lr):
@@ -320,7 +328,8 @@ def cpu_baseline_and_parity(wl, train, pos, alpha, beta, lr, n_blocks, threads):
             "seconds_per_query_wall": wall / nq_s, "mean_candidates_per_query": float(
                 np.mean([b["n_cand"].mean() for b in blocks])),
             "setup_s": setup_s, "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
-    return base, {"origins": origins, "blocks": blocks, "hr": hrs, "dict_margin": oi.margin, "n": od.n}
+    return base, {"origins": origins, "blocks": blocks, "hr": hrs, "n": od.n,
+                  "excluded": block_exclusions(blocks, od, oi, threads)}
 
 
 def cpu_model() -> str:
@@ -346,11 +355,10 @@ def compare_with_oracle(wl, par, nbr_gpu, wgt_gpu, x0_gpu):
     se = 0.0
     npx = 0
     mx = 0.0
-    for (i0, j0), blk, xo in zip(par["origins"], par["blocks"], par["hr"]):
+    for (i0, j0), blk, xo, ex in zip(par["origins"], par["blocks"], par["hr"], par["excluded"]):
         rows = block_rows(wl, i0, j0)
         g = nbr_gpu[rows]
         o = blk["nbr"][:, :K]
-        ex = excluded(blk, par["dict_margin"], K)
         same = (g == o).all(axis=1)
         agree += int((same & ~ex).sum())
         excl += int(ex.sum())
@@ -530,7 +538,9 @@ def run_single(a, wl, config, rank, world, local):
     if par is not None:
         vs_oracle = {"sample": f"{len(par['origins'])} seeded {BLOCK}x{BLOCK} query blocks; HR pixels covered "
                                f"only by a block's patches, before back-projection",
-                     "tolerances": "neighbours bit-exact outside ties (1e-6 rel) and bin-boundary cases (1e-5 w)"}
+                     "tolerances": "neighbours bit-exact outside FP64 ties (1e-6 rel) and queries whose own bins, "
+                                   "or the membership of an entry within their (K+1)-th distance, a projection "
+                                   "within 1e-5 w of a bin boundary makes uncertain"}
         for name, q, prm in (("fp32_exact", q_ex, p_ex), ("bf16", q_bf, p_bf)):
             x0 = Z.reconstruct(ix, q["nbr"], q["wgt"], q["mu"], wl.lr_h, wl.lr_w).cpu().numpy()
             vs_oracle[name] = compare_with_oracle(wl, par, q["nbr"].cpu().numpy(), q["wgt"].cpu().numpy(), x0)

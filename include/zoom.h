@@ -371,9 +371,14 @@ zoom_status zoom_backward(zoom_index ix, const float* lr, int32_t h, int32_t w, 
  * round_up((s*h)*(s*w), 64) + h*w floats of it, larger requests return
  * ZOOM_ERR_INVALID_ARG.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress): make that first call before any
- * stream capture.  All calls share the one array: calls whose work overlaps
- * on the GPU (different streams, or threads without ordering) race; order
- * them on one stream. */
+ * stream capture.  The address is kept for the life of the process, so a
+ * device reset (cudaDeviceReset, or the primary context torn down and made
+ * again) after the first call on that device is not supported.  All calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or threads without ordering) race; order them on one stream.
+ * Errors: INVALID_ARG (NULL pointers, a device index out of range, sizes or
+ * parameters out of range, an image beyond the scratch), CUDA (the runtime
+ * failed, e.g. no device can be counted). */
 #define ZOOM_NOALLOC_SCRATCH_FLOATS (2u * 1024u * 1024u)
 zoom_status zoom_backproject_noalloc(int device, const zoom_degradation* degr, const float* lr,
                                      int32_t h, int32_t w, const zoom_upscale_params* prm,
@@ -386,6 +391,19 @@ zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out);
 /* zoom_set_stage_timing: when enable != 0, zoom_query / zoom_upscale record
  * CUDA events on their stream between stages (zoom_stats.ms_stage). */
 zoom_status zoom_set_stage_timing(zoom_ctx ctx, int32_t enable);
+
+/* zoom_set_fault_injection: a testing aid for the failure paths (the paper
+ * has no counterpart).  Every wait inside the tensor-core filter is bounded:
+ * after wait_limit_ns (0 = the default, 2 s; at most 60 s) it gives up, the
+ * kernel's roles wait for their own copies and MMAs in flight, free their
+ * TMEM and return, and the context's status word reads ZOOM_ERR_TIMEOUT
+ * (zoom_sync_status).  mode 1 makes every filter CTA withhold the release of
+ * its accumulators from the third dictionary tile of its first work item on,
+ * so that such a wait runs out; the call's outputs are then not meaningful,
+ * but reading them is safe (no access leaves its buffer) and the context
+ * stays usable.  mode 0 turns it off.  Applies to later calls on ctx.
+ * Errors: INVALID_ARG for other modes or limits. */
+zoom_status zoom_set_fault_injection(zoom_ctx ctx, int32_t mode, uint64_t wait_limit_ns);
 
 /* zoom_sync_status: synchronises `stream` and reads (then clears) the
  * context's device status word: ZOOM_OK, ZOOM_ERR_TIMEOUT or

@@ -312,6 +312,34 @@ def hash_values(v: np.ndarray, alpha: np.ndarray, beta: np.ndarray, w: float):
     return h, margin
 
 
+def hash_margins(v: np.ndarray, alpha: np.ndarray, beta: np.ndarray, w: float) -> np.ndarray:
+    """Distance of every ratio (alpha.v + beta)/w of Eq. 10 to the nearest
+    integer, per projection: [n][L*k].  A value below 1e-5 marks a projection
+    whose floor an FP32 evaluation may place in the neighbouring bin."""
+    t = np.asarray(v, np.float64) @ np.asarray(alpha, np.float64).T + np.asarray(beta, np.float64)
+    ratio = t / w
+    return np.abs(ratio - np.rint(ratio))
+
+
+def membership_is_certain(hq: np.ndarray, he: np.ndarray, me: np.ndarray, L: int, k: int,
+                          bnd: float = 1e-5) -> bool:
+    """Whether an entry's membership in a query's candidate set (the union of
+    the query's bins over the L tables, Sec. 3.2) survives moving any of the
+    entry's boundary-affected projections (margin me < bnd) to the
+    neighbouring bin.  hq, he: the k*L hash values of the query and the entry;
+    the query's own projections are assumed clear of boundaries."""
+    certain_in = possible_in = False
+    for l in range(L):
+        sl = slice(l * k, (l + 1) * k)
+        eq = hq[sl] == he[sl]
+        near = me[sl] < bnd
+        if eq.all() and not near.any():
+            certain_in = True
+        if (eq | near).all():
+            possible_in = True
+    return certain_in == possible_in
+
+
 def mix64(z):
     """Stafford's variant-13 64-bit finaliser (the SplitMix64 output mixer),
     applied elementwise to uint64 arrays with wrap-around arithmetic."""
@@ -409,6 +437,43 @@ def candidate_set(index: LshIndex, qkeys: np.ndarray, min_hits: int = 1,
     for ids in found:
         hits[ids] += 1
     return np.flatnonzero(hits >= max(min_hits, 1)).astype(np.int64)
+
+
+def neighbour_exclusions(qv: np.ndarray, q_margin: np.ndarray, dist: np.ndarray, d: "Dictionary",
+                         index: "LshIndex", rel: float = 1e-6, bnd: float = 1e-5, feat_norm2=None) -> np.ndarray:
+    """Queries whose K nearest another exact implementation (FP32 keys and
+    distances) may select or order differently, for comparisons with this
+    oracle: (a) a projection of the query within bnd of a bin boundary (its
+    own bins are uncertain, Eq. 10); (b) an entry of the whole dictionary at
+    distance <= the query's (K+1)-th nearest candidate whose membership in the
+    candidate set (Sec. 3.2) is uncertain (``membership_is_certain``); (c) two
+    of the K+1 nearest FP64 distances within rel of each other (the tie rule
+    then decides).  qv [n][D] features, q_margin [n], dist [n][K+1] from
+    ``query`` with K+1 neighbours.  Returns bool [n]."""
+    qv = np.asarray(qv, np.float64)
+    n = qv.shape[0]
+    ex = np.asarray(q_margin) < bnd
+    gaps = np.diff(dist, axis=1)
+    ex |= (gaps <= rel * np.maximum(dist[:, 1:], 1e-30)).any(axis=1)
+    fn = (d.feat * d.feat).sum(axis=1) if feat_norm2 is None else feat_norm2
+    hq_all, _ = hash_values(qv, index.alpha, index.beta, index.w)
+    for i in range(n):
+        if ex[i]:
+            continue
+        D = dist[i, -1]
+        approx = fn - 2.0 * (d.feat @ qv[i]) + qv[i] @ qv[i]
+        idx = np.flatnonzero(approx <= D + 1e-9 * (1.0 + D))
+        exact = ((d.feat[idx] - qv[i]) ** 2).sum(axis=1)
+        idx = idx[exact <= D]
+        if len(idx) == 0:
+            continue
+        he, _ = hash_values(d.feat[idx], index.alpha, index.beta, index.w)
+        me = hash_margins(d.feat[idx], index.alpha, index.beta, index.w)
+        for j in range(len(idx)):
+            if not membership_is_certain(hq_all[i], he[j], me[j], index.L, index.k, bnd):
+                ex[i] = True
+                break
+    return ex
 
 
 def top_k(qv: np.ndarray, cand: np.ndarray, feat: np.ndarray, K: int):

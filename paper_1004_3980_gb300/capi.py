@@ -80,6 +80,7 @@ SIGNATURES = {
                                    _vp]),
     "zoom_get_stats": (C.c_int, [_vp, _vp, _P(Stats)]),
     "zoom_sync_status": (C.c_int, [_vp, _vp]),
+    "zoom_set_fault_injection": (C.c_int, [_vp, C.c_int32, C.c_uint64]),
     "zoom_set_stage_timing": (C.c_int, [_vp, C.c_int32]),
     "zoom_backproject_noalloc": (C.c_int, [C.c_int, _P(Degradation), _vp, _i32, _i32,
                                            _P(UpscaleParams), _vp, _vp]),

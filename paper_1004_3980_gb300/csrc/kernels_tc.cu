@@ -133,17 +133,18 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
   return ok != 0;
 }
 
-// Waits for the phase of `parity` to complete.  Gives up after kWaitNs (or
-// 2^30 polls), or as soon as another role gave up: then it raises the shared
-// abort flag, records ZOOM_ERR_TIMEOUT in the status word and returns false.
+// Waits for the phase of `parity` to complete.  Gives up after limit_ns
+// (kWaitNs unless the context set another limit; or 2^30 polls), or as soon
+// as another role gave up: then it raises the shared abort flag, records
+// ZOOM_ERR_TIMEOUT in the status word and returns false.
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                       unsigned int* status) {
+                                       unsigned int* status, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 0; it < (1u << 30); ++it) {
     if (mbar_try_wait_sleep(bar, parity, 1000000u)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitNs) break;
+    if (globaltimer() - t0 > limit_ns) break;
   }
   *abort_flag = 1;
   atomicExch(status, 1u);
@@ -151,8 +152,20 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
 }
 // The common case inline: one poll, then the bounded slow path.
 __device__ __forceinline__ bool mbar_wait_fast(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                               unsigned int* status) {
-  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag, status);
+                                               unsigned int* status, uint64_t limit_ns) {
+  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort_flag, status, limit_ns);
+}
+// Before a CTA exits, also after an abort: waits for an asynchronous
+// operation it started (a bulk copy, or the MMAs a commit tracks) to signal
+// its barrier, whatever the abort flag says, for at most kWaitNs.
+__device__ __noinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, unsigned int* status) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+    if (globaltimer() - t0 > kWaitNs) break;
+  }
+  atomicExch(status, 1u);
+  return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -288,6 +301,11 @@ struct TcArgs {
   // nq_dev != nullptr: only the first min(*nq_dev, nq) queries are searched
   // (a count written by an earlier kernel); nq stays the lists' row stride
   const unsigned long long* nq_dev;
+  // bound on every wait (ns), and the testing aid: inject == 1 makes each
+  // CTA's epilogue withhold the release of its accumulators from the third
+  // tile of its first item on, so the issuing threads' waits run out
+  uint64_t wait_ns;
+  int inject;
 };
 
 // Queries searched: nq, or the device count when one is given (read where
@@ -399,7 +417,8 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
   // columns go back to the MMA as soon as its 4 epilogue warps have read them
   uint64_t* acc_full = b_empty + kStages;      // [2][2]
   uint64_t* acc_empty = acc_full + 4;          // [2][2]
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 4);
+  uint64_t* drain = acc_empty + 4;             // [4] one per MMA-issuing thread, at exit
+  uint32_t* tmem_slot = (uint32_t*)(drain + 4);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   constexpr int kBuf = tc_buf(KC);
   float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBuf][256]
@@ -418,6 +437,7 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
     for (int b = 0; b < 4; ++b) {
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, 128);
+      mbar_init(drain + b, 1);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -438,27 +458,36 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
       int stage = 0;
       uint32_t phase = 0, a_phase = 0;
       bool first = true;
+      int a_copies = 0;
+      int64_t b_copies = 0;
       WorkIter it;
       int qp, seg, t0, t1;
       while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
         if (!first) {
-          if (!mbar_wait(a_empty, a_phase, abort_flag, a.status)) break;
+          if (!mbar_wait(a_empty, a_phase, abort_flag, a.status, a.wait_ns)) break;
           a_phase ^= 1u;
         }
         first = false;
         mbar_arrive_expect_tx(a_full, 2 * kTileBytes);
         bulk_g2s(sA, (const unsigned char*)a.qop + (size_t)qp * 2 * kTileBytes, 2 * kTileBytes, a_full);
+        ++a_copies;
         for (int t = t0; t < t1; ++t) {
-          if (!mbar_wait_fast(b_empty + stage, phase ^ 1u, abort_flag, a.status)) break;
+          if (!mbar_wait_fast(b_empty + stage, phase ^ 1u, abort_flag, a.status, a.wait_ns)) break;
           mbar_arrive_expect_tx(b_full + stage, kTileBytes);
           bulk_g2s(sB + stage * kTileBytes, (const unsigned char*)a.dop + (size_t)t * kTileBytes,
                    kTileBytes, b_full + stage);
+          ++b_copies;
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
         }
       }
+      // no bulk copy may still be writing into shared memory at exit: wait
+      // for the last query-tile copy and the last copy into every ring stage
+      if (a_copies > 0) mbar_drain(a_full, (uint32_t)(a_copies - 1) & 1u, a.status);
+      for (int64_t i = b_copies - kStages > 0 ? b_copies - kStages : 0; i < b_copies; ++i)
+        mbar_drain(b_full + i % kStages, (uint32_t)(i / kStages) & 1u, a.status);
     }
   } else if (warp == 1 || warp >= 10) {
     // ------- MMA issue: one thread per query tile (and buffer, kMma = 4) -------
@@ -480,14 +509,14 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
       WorkIter it;
       int qp, seg, t0, t1;
       while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
-        if (!mbar_wait_fast(a_full, a_phase, abort_flag, a.status)) break;
+        if (!mbar_wait_fast(a_full, a_phase, abort_flag, a.status, a.wait_ns)) break;
         a_phase ^= 1u;
         tc_fence_after();
         bool ok = true;
         for (int t = t0; t < t1; ++t) {
           if (mine_buf < 0 || buf == mine_buf) {
-            if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status) ||
-                !mbar_wait_fast(acc_empty + buf * 2 + qt, accp[buf] ^ 1u, abort_flag, a.status)) {
+            if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status, a.wait_ns) ||
+                !mbar_wait_fast(acc_empty + buf * 2 + qt, accp[buf] ^ 1u, abort_flag, a.status, a.wait_ns)) {
               ok = false;
               break;
             }
@@ -511,8 +540,12 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
         if (!ok) break;
       }
       // the last item's release of the query tiles is never consumed by the
-      // producer: wait for it so no tensor-core arrival is pending at exit
-      if (items > 0) mbar_wait(a_empty, (uint32_t)(items - 1) & 1u, abort_flag, a.status);
+      // producer: wait for it so no tensor-core arrival is pending at exit;
+      // then (also after an abort) one more commit, whose arrival means every
+      // MMA this thread issued has completed before TMEM is freed
+      if (items > 0) mbar_drain(a_empty, (uint32_t)(items - 1) & 1u, a.status);
+      mma_commit(drain + m);
+      mbar_drain(drain + m, 0u, a.status);
     }
   } else {
     // ------------- epilogue: per query, the MC best 32-entry chunks -------------
@@ -532,8 +565,10 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
     const bool releaser = (ew & 3) == 0 && lane == 0;
     WorkIter it;
     int qp, split, t0, t1;
+    int item_no = 0;
     while (it.next(a, qp, split, t0, t1)) {
       if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
+      const bool withhold = a.inject == 1 && item_no++ == 0;   // testing aid (see TcArgs)
       const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
       const bool valid = q < searched_queries(a);
       const float qn = valid ? a.qn[q] : 0.f;
@@ -576,7 +611,7 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
       for (int t = t0; t < t1; ++t) {
         // every lane polls, then the warp agrees (and reconverges) before the
         // warp-collective TMEM loads
-        const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status));
+        const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + buf * 2 + qt, accp[buf], abort_flag, a.status, a.wait_ns));
         if (!w) {
           ok = false;
           break;
@@ -598,7 +633,8 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
           tmem_regs_ready(vc, mc);
           tmem_regs_ready(vd, md);
           tc_fence_before();
-          mbar_arrive(acc_empty + buf * 2 + qt);   // every TMEM read of this tile is done
+          if (!withhold || t < t0 + 2)
+            mbar_arrive(acc_empty + buf * 2 + qt);   // every TMEM read of this tile is done
           chunk_test(ma, t * 4, thr, bv, bi, cnt);
           chunk_test(mb, t * 4 + 1, thr, bv, bi, cnt);
           chunk_test(mc, t * 4 + 2, thr, bv, bi, cnt);
@@ -613,7 +649,7 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
             tmem_regs_ready(vb, mb);
             if (h == 1) {   // every TMEM read of this tile is done: hand the buffer back
               tc_fence_before();
-              mbar_arrive(acc_empty + buf * 2 + qt);
+              if (!withhold || t < t0 + 2) mbar_arrive(acc_empty + buf * 2 + qt);
             }
             chunk_test(ma, t * 4 + 2 * h, thr, bv, bi, cnt);
             chunk_test(mb, t * 4 + 2 * h + 1, thr, bv, bi, cnt);
@@ -1233,8 +1269,10 @@ static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cuda
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
                           int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
                           float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st,
-                          const unsigned long long* nq_dev) {
+                          const unsigned long long* nq_dev, uint64_t wait_ns, int inject) {
   TcArgs a;
+  a.wait_ns = wait_ns > 0 ? wait_ns : kWaitNs;
+  a.inject = inject;
   a.qop = qop;
   a.qn = qn;
   a.dop = dop;

@@ -636,7 +636,8 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
   zoom_stage_mark(ctx, 8, st);   // start of the tensor-core filter kernel
   if (e == cudaSuccess)
     e = launch_knn_tc(qop, qn, nq, pl.prec == 0 ? ix->dop16 : pl.prec == 1 ? ix->dopbf : ix->dopf1, d->n, pl.prec,
-                      pl.KCH / 8, pl.MC, pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st);
+                      pl.KCH / 8, pl.MC, pl.nsplit, pl.tail_split, ctx->n_sm, ld, li, ctx->d_status, st, nullptr,
+                      ctx->wait_ns, ctx->inject);
   zoom_stage_mark(ctx, 9, st);   // end of the filter kernel
   if (e == cudaSuccess)
     e = launch_rerank(d->d, pl.MC, K, b.feat, d->dpad, qn, b.keys, nq, d->feat, ix->dkeys, d->n, ix->L,
@@ -660,7 +661,7 @@ cudaError_t run_search_ws(zoom_index ix, const zoom_upscale_params* prm, const Q
       e = launch_operand(cfeat, d->dpad, d->d, pl.cap2, pl.q_rows2, 0, 0, cqop, cqn, st, cnt);
     if (e == cudaSuccess)
       e = launch_knn_tc(cqop, cqn, pl.cap2, ix->dop16, d->n, 0, tc_kc(d->d, 0), pl.MC2, pl.nsplit2, 0, ctx->n_sm,
-                        ld2, li2, ctx->d_status, st, cnt);
+                        ld2, li2, ctx->d_status, st, cnt, ctx->wait_ns, ctx->inject);
     if (e == cudaSuccess)
       e = launch_rerank(d->d, pl.MC2, K, cfeat, d->dpad, cqn, ckeys, pl.cap2, d->feat, ix->dkeys, d->n, ix->L,
                         ix->t, ld2, li2, pl.nsplit2, 1, b.nbr, b.dist, fb2, cnt + 1, st, fb, cnt);
@@ -924,6 +925,15 @@ zoom_status zoom_get_stats(zoom_ctx ctx, void* stream, zoom_stats* out) {
 zoom_status zoom_set_stage_timing(zoom_ctx ctx, int32_t enable) {
   if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL context");
   ctx->stage_timing = enable != 0;
+  return ZOOM_OK;
+}
+
+zoom_status zoom_set_fault_injection(zoom_ctx ctx, int32_t mode, uint64_t wait_limit_ns) {
+  if (!ctx) return fail(ZOOM_ERR_INVALID_ARG, "NULL context");
+  if (mode < 0 || mode > 1) return fail(ZOOM_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (wait_limit_ns > 60000000000ull) return fail(ZOOM_ERR_INVALID_ARG, "wait_limit_ns above 60 s");
+  ctx->inject = mode;
+  ctx->wait_ns = wait_limit_ns;
   return ZOOM_OK;
 }
 

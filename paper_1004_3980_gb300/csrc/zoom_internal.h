@@ -41,6 +41,8 @@ struct zoom_ctx_s {
   bool stage_rec[kStageEvents] = {};
   void* batch = nullptr;          // recorded batch (graph, workspace, events): zoom_api.cu
   void* tuned = nullptr;          // autotuned search choices: zoom_api.cu
+  uint64_t wait_ns = 0;           // bound on the tensor-core filter's waits (0: 2 s)
+  int inject = 0;                 // testing aid: zoom_set_fault_injection
 };
 
 // Records the boundary event of stage `i` when stage timing is on.
@@ -155,10 +157,12 @@ int tc_list_size(int precision, int K, int rerank_mult);
 // tail_split > 0: whole query pairs round robin for the full rounds over the
 // grid, the remaining pairs cut into tail_split dictionary parts (nsplit must
 // equal tail_split); 0: nsplit round-robin splits of every pair
+// wait_ns: bound on every device wait (0: 2 s); inject: testing aid (1: the
+// epilogue withholds its accumulator releases, so a wait runs out)
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,
                           int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
                           float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st,
-                          const unsigned long long* nq_dev = nullptr);
+                          const unsigned long long* nq_dev = nullptr, uint64_t wait_ns = 0, int inject = 0);
 // ld/li: per split and query the MC best 32-entry chunks (filter minimum d~,
 // chunk index), ascending; form 1 for the FP16-split filter, 2 for the
 // single-term FP16 filter (both: proof and fallback flags), 0 for the BF16

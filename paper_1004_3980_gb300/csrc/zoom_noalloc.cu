@@ -50,9 +50,13 @@ extern "C" zoom_status zoom_backproject_noalloc(int device, const zoom_degradati
     return ZOOM_ERR_INVALID_ARG;
   }
   int n_dev = 0;
-  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev ||
-      device >= kMaxDevices) {
+  const cudaError_t ec = cudaGetDeviceCount(&n_dev);
+  if (ec != cudaSuccess) {   // no driver, or a sticky error of the runtime: not an argument error
     cudaGetLastError();
+    zoom_set_error(std::string("cudaGetDeviceCount: ") + cudaGetErrorString(ec));
+    return ZOOM_ERR_CUDA;
+  }
+  if (device < 0 || device >= n_dev || device >= kMaxDevices) {
     zoom_set_error("no such device");
     return ZOOM_ERR_INVALID_ARG;
   }

@@ -74,12 +74,18 @@ class UpscaleParams:
 
 class Context:
     """A library context on one CUDA device; device scratch memory comes from
-    PyTorch's caching allocator."""
+    PyTorch's caching allocator, or from `allocator` (an object with methods
+    alloc(nbytes, stream, user) -> device pointer or None, and
+    free(ptr, nbytes, stream, user)), or -- torch_allocator=False and no
+    allocator -- from cudaMallocAsync inside the library."""
 
-    def __init__(self, device: int = 0, torch_allocator: bool = True):
+    def __init__(self, device: int = 0, torch_allocator: bool = True, allocator=None):
         self.device = device
         alloc = None
-        if torch_allocator:
+        if allocator is not None:
+            self._cb = (capi.ALLOC_FN(allocator.alloc), capi.FREE_FN(allocator.free))
+            alloc = capi.Allocator(self._cb[0], self._cb[1], None)
+        elif torch_allocator:
             def _a(nbytes, stream, user):
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
@@ -110,6 +116,12 @@ class Context:
 
     def sync_status(self, stream=None) -> None:
         capi.call("zoom_sync_status", self.handle, _stream(stream))
+
+    def set_fault_injection(self, mode: int, wait_limit_ns: int = 0) -> None:
+        """Testing aid (zoom_set_fault_injection): mode 1 makes the
+        tensor-core filter's bounded waits run out; wait_limit_ns bounds them
+        (0: the default 2 s)."""
+        capi.call("zoom_set_fault_injection", self.handle, int(mode), int(wait_limit_ns))
 
     def close(self):
         if getattr(self, "handle", None):

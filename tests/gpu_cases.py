@@ -5,6 +5,8 @@ from __future__ import annotations
 
 import dataclasses
 import functools
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -85,3 +87,12 @@ def tie_or_boundary(oq: O.QueryResult, K: int, dict_margin: np.ndarray, rel: flo
     ex |= (gaps <= rel * scale).any(axis=1)
     assert ex.shape == (n,)
     return ex
+
+
+def oracle_rows(lr, od, oix, K, reg_rel, rows):
+    """O.query on the given query rows, split over the host threads."""
+    parts = np.array_split(np.asarray(rows), max(1, min(len(rows), os.cpu_count() or 1)))
+    with ThreadPoolExecutor(max_workers=len(parts)) as ex:
+        res = list(ex.map(lambda r: O.query(lr, od, oix, K, reg_rel, rows=r), parts))
+    cat = lambda f: np.concatenate([getattr(q, f) for q in res])
+    return O.QueryResult(*(cat(f.name) for f in dataclasses.fields(O.QueryResult)))

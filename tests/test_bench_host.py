@@ -106,7 +106,8 @@ def test_oracle_blocks_equal_the_whole_image_oracle():
     fw, lw = bench.covered_window(wl, *origins[0])
     np.testing.assert_allclose(xb[lw], x0[fw], atol=1e-12)
     # the comparison of a GPU-shaped result (here the oracle's own) is exact
-    par = {"origins": origins, "blocks": blocks, "hr": [xb], "dict_margin": oi.margin}
+    par = {"origins": origins, "blocks": blocks, "hr": [xb],
+           "excluded": bench.block_exclusions(blocks, od, oi, 2)}
     c = bench.compare_with_oracle(wl, par, qr.nbr, qr.wgt, x0)
     assert c["identical_neighbours"] + c["excluded_tie_or_boundary"] == c["queries"] == bench.BLOCK ** 2
     assert c["recall"] == 1.0 and c["max_abs"] < 1e-12 and c["weights_max_abs"] < 1e-12

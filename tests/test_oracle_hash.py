@@ -5,6 +5,7 @@ import math
 import numpy as np
 import pytest
 
+import synth_inputs as S
 from oracle import zoom_oracle as O
 
 
@@ -156,3 +157,33 @@ def test_candidate_cap_takes_tables_in_order():
     assert O.candidate_set(idx, qk, max_candidates=4).tolist() == [1, 3, 5, 9]
     assert O.candidate_set(idx, qk, max_candidates=2).tolist() == [1, 5]
     assert O.candidate_set(idx, qk).tolist() == [1, 3, 5, 7, 9]
+
+
+def test_membership_certainty_of_boundary_entries():
+    # L = 2 tables of k = 3 values; the entry matches the query's bin in
+    # table 0 only where a near-boundary value flips
+    L, k = 2, 3
+    hq = np.array([1, 2, 3, 7, 7, 7])
+    far = np.ones(6)
+    # equal in table 0, no near values: a certain member
+    assert O.membership_is_certain(hq, np.array([1, 2, 3, 0, 0, 0]), far, L, k)
+    # differs everywhere by a clear value: certainly not a member
+    assert O.membership_is_certain(hq, np.array([1, 2, 4, 0, 7, 7]), far, L, k)
+    # differs in table 0 only at a near-boundary value: may flip in
+    m = far.copy()
+    m[2] = 1e-7
+    assert not O.membership_is_certain(hq, np.array([1, 2, 4, 0, 7, 7]), m, L, k)
+    # equal in table 0 with a near value, but a certain member via table 1
+    m = far.copy()
+    m[0] = 1e-7
+    assert O.membership_is_certain(hq, np.array([1, 2, 3, 7, 7, 7]), m, L, k)
+    # equal in table 0 only, with a near value: may flip out
+    assert not O.membership_is_certain(hq, np.array([1, 2, 3, 7, 7, 6]), m, L, k)
+
+
+def test_hash_margins_agree_with_hash_values(rng):
+    v = rng.normal(size=(50, 9))
+    a, b = S.lsh_draws(5, 3, 4, 9, 4.0)
+    h, margin = O.hash_values(v, a, b, 4.0)
+    mm = O.hash_margins(v, a, b, 4.0)
+    np.testing.assert_array_equal(mm.min(axis=1), margin)

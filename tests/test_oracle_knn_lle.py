@@ -116,3 +116,36 @@ def test_lle_permutation_invariant(rng):
     p = rng.permutation(8)
     wp, _ = O.lle_weights(q, nb[p], 1e-3, 1.0)
     np.testing.assert_allclose(wp, w[p], atol=1e-12)
+
+
+def test_neighbour_exclusions_flag_ties_boundaries_and_uncertain_members():
+    # tiny dictionary: the exclusion rule agrees with a brute-force reading
+    # of its three conditions
+    import synth_inputs as S
+    g = np.random.default_rng(4)
+    N, D, L, k, K = 400, 9, 3, 4, 3
+    feat = g.normal(scale=0.4, size=(N, D))
+    feat[7] = feat[3]                                     # an exact duplicate: a distance tie
+    d = O.Dictionary(2, 3, None, feat, None, None)
+    a, b = S.lsh_draws(6, L, k, D, 1.0)
+    ix = O.build_index(d, a, b, 1.0, L, k)
+    q = np.vstack([feat[3] + 1e-3, g.normal(scale=0.4, size=(40, D))])
+    hq, qm = O.hash_values(q, a, b, 1.0)
+    nb = np.zeros((len(q), K + 1), np.int64)
+    dist = np.zeros((len(q), K + 1))
+    for i in range(len(q)):
+        keys = O.fold_keys(hq[i:i + 1], L, k)[0]
+        nb[i], dist[i], _ = O.top_k(q[i], O.candidate_set(ix, keys), feat, K + 1)
+    ex = O.neighbour_exclusions(q, qm, dist, d, ix)
+    assert ex[0]                                          # the tie
+    # brute force of condition (b) with a loose boundary (1e-2): more entries
+    # become uncertain, never fewer queries
+    ex_loose = O.neighbour_exclusions(q, qm, dist, d, ix, bnd=1e-2)
+    assert (ex_loose >= ex).all() and ex_loose.sum() > ex.sum()
+    for i in np.flatnonzero(ex_loose & ~ex):
+        dd = ((feat - q[i]) ** 2).sum(axis=1)
+        close = np.flatnonzero(dd <= dist[i, -1])
+        he, _ = O.hash_values(feat[close], a, b, 1.0)
+        me = O.hash_margins(feat[close], a, b, 1.0)
+        assert qm[i] < 1e-2 or any(not O.membership_is_certain(hq[i], he[j], me[j], L, k, 1e-2)
+                                   for j in range(len(close)))

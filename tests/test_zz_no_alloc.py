@@ -59,3 +59,35 @@ def test_noalloc_refuses_images_beyond_its_scratch():
                                       C.c_void_p(out.data_ptr()), None)
     assert rc == 1
     assert b"too large" in lib.zoom_last_error()
+
+
+@pytest.mark.parametrize("h,w,accepted", [
+    (1024, 1024, True),    # scale 1: 1 Mi HR floats + 1 Mi LR floats = the maximum exactly
+    (1023, 1025, True),    # 1,048,575 HR floats round up to 1 Mi before the LR image: 2 Mi - 1
+    (1024, 1025, False),   # one column more: 2 Mi + 2048
+])
+def test_noalloc_scratch_limit_is_exact(h, w, accepted):
+    # the size check at its boundary: round_up(s^2 h w, 64) + h w floats
+    # against ZOOM_NOALLOC_SCRATCH_FLOATS = 2 Mi; accepted sizes give the
+    # allocating entry point's output
+    from paper_1004_3980_gb300 import capi
+    import paper_1004_3980_gb300 as Z
+    lib = capi.lib()
+    need = (h * w + 63) // 64 * 64 + h * w
+    assert (need <= 2 * 1024 * 1024) == accepted
+    y = torch.from_numpy(S.make_image(77, h, w)).cuda()
+    x0 = torch.from_numpy(S.make_image(78, h, w)).cuda()
+    p = Z.UpscaleParams(bp_iters=2)
+    out = x0.clone()
+    degr = capi.Degradation(1, 1, 0.8)
+    prm = p.c()
+    rc = lib.zoom_backproject_noalloc(0, C.byref(degr), C.c_void_p(y.data_ptr()), h, w, C.byref(prm),
+                                      C.c_void_p(out.data_ptr()), None)
+    if not accepted:
+        assert rc == 1 and b"too large" in lib.zoom_last_error()
+        return
+    assert rc == 0, lib.zoom_last_error()
+    ref = x0.clone()
+    Z.backproject(Z.Context(0), y, ref, 1, p)
+    torch.cuda.synchronize()
+    assert torch.max(torch.abs(out - ref)).item() <= 1e-6
