@@ -85,6 +85,10 @@ typedef struct {
 /* LSH parameters (Sec. 3.2, Sec. 4.1).  L tables of k concatenated hashes
  * h = floor((alpha.v + beta) / w).  min_table_hits = t (an ID is a candidate
  * if it shares the query's bin in >= t tables; 1 = plain union).
+ * proj_dist and seed: how zoom_build_index draws alpha and beta when the
+ * caller passes none (zoom_lsh_draws): proj_dist 0 = Gaussian vectors, 1 =
+ * Cauchy vectors by the rule of Eq. 11 (a / b, a and b standard normal,
+ * |b| >= 1e-3), from the 64-bit seed.
  * max_candidates: 0 = no cap; > 0 = the early stop of Sec. 4.2 (tables in
  * order, IDs ascending within a bin, stop at exactly max_candidates distinct
  * IDs; t is then not used).  With a cap the K nearest are searched among
@@ -99,6 +103,8 @@ typedef struct {
   float w;
   int32_t min_table_hits;
   int32_t max_candidates;
+  int32_t proj_dist;
+  uint64_t seed;
 } zoom_lsh_params;
 
 /* Inference parameters.  K nearest neighbours (1..16); reg_rel: the LLE
@@ -169,7 +175,10 @@ const char* zoom_last_error(void);
  * image is rounded once to float32); pair n uses positions[n] = (image m,
  * LR row i, LR col j) (host int32 [n_pairs][3]): LR patch at (i, j) and HR
  * patch at (s*i, s*j).  Pair n gets ID n; positions should be sorted by
- * (m, i, j) so that IDs follow the paper's row order.  Stored per pair:
+ * (m, i, j) so that IDs follow the paper's row order.  positions == NULL:
+ * the library draws them from `seed` (zoom_sample_positions: uniform without
+ * replacement over every LR patch origin of the images, in origin order);
+ * otherwise seed is not used.  Stored per pair:
  * the LR pixels, the LR mean mu, the feature (degr->feature; gradients are
  * taken on the whole LR training image) and the HR patch minus mu.  Errors:
  * INVALID_ARG for sizes out of range or positions whose patch leaves its
@@ -177,7 +186,7 @@ const char* zoom_last_error(void);
 zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
                                   const int32_t* heights, const int32_t* widths,
                                   int32_t n_images, const zoom_degradation* degr,
-                                  int64_t n_pairs, const int32_t* positions,
+                                  int64_t n_pairs, const int32_t* positions, uint64_t seed,
                                   void* stream, zoom_dict* out);
 void zoom_dict_destroy(zoom_dict d);
 /* Copies stored arrays to the host (synchronises `stream`): lr_pix [N][P*P],
@@ -212,12 +221,40 @@ zoom_status zoom_sample_crops(zoom_ctx ctx, const float* const* images, const in
                               int32_t draws_per_image, int32_t crop_h, int32_t crop_w,
                               int32_t* windows, float* crops, void* stream);
 
+/* ---- seeded random draws (host, no device work) ---------------------------
+ * Both come from the counter-based generator Philox4x32-10 (Salmon et al.,
+ * SC 2011) keyed by the 64-bit seed; a draw is a function of (seed, its
+ * counter) alone.
+ * zoom_lsh_draws: the draws of Eq. 10 for feature dimension dim: alpha
+ * (host float32 [L*k][dim]) element n is the Box-Muller normal (FP64, cosine
+ * branch, uniforms (x + 1/2) / 2^32) of counter (n, 0, 0, 0); with
+ * lsh->proj_dist 1 it is divided by the normal of counter (n, t, 1, 0) for
+ * the first t = 0, 1, ... with |b| >= 1e-3 (Eq. 11).  beta (host float32
+ * [L*k]): u * w, u the uniform of the first word of counter (j, 0, 0, 1),
+ * kept below w.  Errors: INVALID_ARG (NULL, L or k outside 1..32, dim
+ * outside 1..64, w <= 0, another proj_dist). */
+zoom_status zoom_lsh_draws(const zoom_lsh_params* lsh, int32_t dim, float* alpha, float* beta);
+/* zoom_sample_positions: n_pairs dictionary positions (host int32
+ * [n_pairs][3] = (image, LR row, LR col)) drawn uniformly without
+ * replacement over every lr_patch x lr_patch origin of n_images LR images of
+ * lr_heights[m] x lr_widths[m] (origins numbered image by image, row by
+ * row): origin o draws the 64-bit key (first word high) of counter
+ * (o, 0, 0, 2), the n_pairs smallest (key, o) are kept, in origin order (the
+ * paper's row-order IDs, Sec. 2.1).  For HR training images the LR sizes
+ * are the HR sizes divided by the scale.  Errors: INVALID_ARG (NULL, an
+ * image smaller than a patch, n_pairs outside 1..number of origins). */
+zoom_status zoom_sample_positions(uint64_t seed, int32_t n_images, const int32_t* lr_heights,
+                                  const int32_t* lr_widths, int32_t lr_patch, int64_t n_pairs,
+                                  int32_t* positions);
+
 /* ---- LSH index (Sec. 3.2; Sec. 4.1, Eq. 10) -----------------------------
  * Hashes every dictionary feature into L tables.  alpha: host float32
- * [L*k][D] projection vectors (D the feature dimension); beta: host float32 [L*k] offsets in
- * [0, w) (the random draws are inputs).  Builds, per table, the bucket key
- * of every entry and a CSR of its bins (keys radix-sorted on the device).
- * Errors: INVALID_ARG for parameters out of range. */
+ * [L*k][D] projection vectors (D the feature dimension); beta: host float32
+ * [L*k] offsets in [0, w).  Both NULL: the library draws them from
+ * lsh->seed and lsh->proj_dist (zoom_lsh_draws).  Builds, per table, the
+ * bucket key of every entry and a CSR of its bins (keys radix-sorted on the
+ * device).  Errors: INVALID_ARG for parameters out of range or only one of
+ * alpha and beta given. */
 zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const float* alpha,
                              const float* beta, void* stream, zoom_index* out);
 void zoom_index_destroy(zoom_index ix);
@@ -225,7 +262,8 @@ void zoom_index_destroy(zoom_index ix);
  * n_bins != NULL, the number of bins per table to host int32 [L]
  * (synchronises `stream`). */
 zoom_status zoom_index_export(zoom_index ix, uint64_t* keys, int32_t* n_bins, void* stream);
-/* The index's LSH parameters (any pointer may be NULL). */
+/* The index's LSH parameters (any pointer may be NULL); proj_dist and seed
+ * are those of the library's draws, 0 when the caller gave alpha and beta. */
 zoom_status zoom_index_info(zoom_index ix, zoom_lsh_params* lsh);
 
 /* ---- files: checkpoint / resume ------------------------------------------

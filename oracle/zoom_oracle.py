@@ -294,6 +294,111 @@ def crop_windows(rows, cols, h: int, w: int, ch: int, cw: int):
 
 
 # ---------------------------------------------------------------------------
+# Seeded random draws: projections (Eq. 10-11) and dictionary positions
+# (Sec. 5.1), from the counter-based generator Philox4x32-10 of Salmon,
+# Moraes, Dror and Shaw ("Parallel random numbers: as easy as 1, 2, 3", SC
+# 2011), written from its published definition.
+# ---------------------------------------------------------------------------
+
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)     # round multipliers
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)     # key schedule (Weyl) increments
+CAUCHY_EPS = 1e-3                       # |b| >= eps in Eq. 11 (the paper gives no value)
+
+
+def philox4x32_10(ctr: np.ndarray, seed: int) -> np.ndarray:
+    """Philox4x32 with 10 rounds for counters ctr uint32 [n][4] under the
+    64-bit key `seed` (low word first).  One round maps (c0, c1, c2, c3) to
+    (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key
+    gains the Weyl increments before every round but the first.  Returns
+    uint32 [n][4]."""
+    c = np.asarray(ctr, np.uint64).reshape(-1, 4).copy()
+    k0, k1 = np.uint64(seed & 0xFFFFFFFF), np.uint64((seed >> 32) & 0xFFFFFFFF)
+    m0, m1 = np.uint64(PHILOX_M[0]), np.uint64(PHILOX_M[1])
+    lo32 = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + np.uint64(PHILOX_W[0])) & lo32
+            k1 = (k1 + np.uint64(PHILOX_W[1])) & lo32
+        p0 = m0 * c[:, 0]
+        p1 = m1 * c[:, 2]
+        c = np.stack([(p1 >> np.uint64(32)) ^ c[:, 1] ^ k0, p1 & lo32,
+                      (p0 >> np.uint64(32)) ^ c[:, 3] ^ k1, p0 & lo32], axis=1)
+    return c.astype(np.uint32)
+
+
+def _unit(x: np.ndarray) -> np.ndarray:
+    """A 32-bit word to a uniform value in (0, 1): (x + 1/2) / 2^32."""
+    return (np.asarray(x, np.float64) + 0.5) * 2.0 ** -32
+
+
+def _normal(words: np.ndarray) -> np.ndarray:
+    """Box-Muller (cosine branch) from the first two words of each counter's
+    output, in FP64: sqrt(-2 ln u1) cos(2 pi u2)."""
+    u1, u2 = _unit(words[:, 0]), _unit(words[:, 1])
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def _ctr(n, c1=0, c2=0, c3=0) -> np.ndarray:
+    n = np.asarray(n, np.uint64)
+    out = np.zeros((n.size, 4), np.uint64)
+    out[:, 0] = n & np.uint64(0xFFFFFFFF)
+    out[:, 1] = (n >> np.uint64(32)) + np.uint64(c1)
+    out[:, 2] = c2
+    out[:, 3] = c3
+    return out
+
+
+def projection_draws(seed: int, L: int, k: int, D: int, w: float, dist: int = 0, eps: float = CAUCHY_EPS):
+    """The random draws of Eq. 10 from `seed`: alpha float32 [L*k][D] and beta
+    float32 [L*k].  Element n (row-major) of alpha: dist 0 (Gaussian, the
+    workloads') the normal of counter (n, 0, 0, 0); dist 1 (Cauchy, Eq. 11)
+    a / b, a that normal and b the normal of counter (n, t, 1, 0) for the
+    first t = 0, 1, ... with |b| >= eps.  beta_j = u w, u from counter
+    (j, 0, 0, 1), kept below w after rounding to float32."""
+    n = L * k * D
+    a = _normal(philox4x32_10(_ctr(np.arange(n)), seed))
+    if dist == 1:
+        b = np.empty(n)
+        todo = np.arange(n)
+        t = 0
+        while todo.size:
+            bt = _normal(philox4x32_10(_ctr(todo, c1=t, c2=1), seed))
+            ok = np.abs(bt) >= eps
+            b[todo[ok]] = bt[ok]
+            todo = todo[~ok]
+            t += 1
+        a = a / b
+    elif dist != 0:
+        raise ValueError("dist must be 0 (Gaussian) or 1 (Cauchy)")
+    alpha = a.astype(np.float32).reshape(L * k, D)
+    beta = (_unit(philox4x32_10(_ctr(np.arange(L * k), c3=1), seed)[:, 0]) * w).astype(np.float32)
+    beta = np.minimum(beta, np.nextafter(np.float32(w), np.float32(0.0)))
+    return alpha, beta
+
+
+def sample_positions_seeded(seed: int, lr_sizes, P: int, n_pairs: int) -> np.ndarray:
+    """Dictionary positions (Sec. 2.1, Sec. 5.1), uniform without replacement
+    over every P x P patch origin of every LR training image (origins numbered
+    image by image, row by row): origin o draws the 64-bit key (w0, w1) of
+    counter (o, 0, 0, 2); the n_pairs origins with the smallest (key, o) are
+    kept, in origin order, so that a position's rank is its ID.  lr_sizes:
+    (h, w) per image.  Returns int32 [n_pairs][3] = (image, row, col)."""
+    counts = [(h - P + 1) * (w - P + 1) for h, w in lr_sizes]
+    total = int(sum(counts))
+    if not 0 < n_pairs <= total:
+        raise ValueError("n_pairs must be in 1..number of origins")
+    words = philox4x32_10(_ctr(np.arange(total), c3=2), seed).astype(np.uint64)
+    key = (words[:, 0] << np.uint64(32)) | words[:, 1]
+    order = np.lexsort((np.arange(total), key))
+    chosen = np.sort(order[:n_pairs])
+    starts = np.cumsum([0] + counts)
+    img = np.searchsorted(starts, chosen, side="right") - 1
+    rem = chosen - starts[img]
+    nw = np.array([w - P + 1 for _, w in lr_sizes])[img]
+    return np.stack([img, rem // nw, rem % nw], axis=1).astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
 # Hashing (Sec. 3.2; Sec. 4.1, Eq. 10)
 # ---------------------------------------------------------------------------
 

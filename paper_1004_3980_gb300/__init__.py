@@ -9,4 +9,4 @@ include/zoom.h); this package only marshals arguments.
 from .zoom import (Context, DegradeFunction, Dictionary, Index, ReconstructFunction,  # noqa: F401
                    UpscaleParams, backproject, degrade, degrade_adjoint, dictionary_hr,
                    map_energy_grads, query, reconstruct, reconstruct_adjoint, reconstruct_with,
-                   sample_crops, upscale, upscale_batch, batch_release)
+                   sample_crops, upscale, upscale_batch, batch_release, lsh_draws, sample_positions)

@@ -34,6 +34,7 @@ SOURCES = [
     "zoom_api_backward.cu",
     "zoom_io.cu",
     "zoom_sample.cu",
+    "zoom_random.cu",
 ]
 HEADERS = ["zoom_internal.h", "device_common.cuh", "knn_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

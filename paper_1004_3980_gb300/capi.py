@@ -29,7 +29,8 @@ class Degradation(C.Structure):
 
 class LshParams(C.Structure):
     _fields_ = [("L", C.c_int32), ("k", C.c_int32), ("w", C.c_float),
-                ("min_table_hits", C.c_int32), ("max_candidates", C.c_int32)]
+                ("min_table_hits", C.c_int32), ("max_candidates", C.c_int32),
+                ("proj_dist", C.c_int32), ("seed", C.c_uint64)]
 
 
 class UpscaleParams(C.Structure):
@@ -57,7 +58,9 @@ SIGNATURES = {
     "zoom_status_string": (C.c_char_p, [C.c_int]),
     "zoom_last_error": (C.c_char_p, []),
     "zoom_build_dictionary": (C.c_int, [_vp, _P(_vp), _P(_i32), _P(_i32), _i32, _P(Degradation),
-                                        _i64, _P(_i32), _vp, _P(_vp)]),
+                                        _i64, _P(_i32), C.c_uint64, _vp, _P(_vp)]),
+    "zoom_lsh_draws": (C.c_int, [_P(LshParams), _i32, _vp, _vp]),
+    "zoom_sample_positions": (C.c_int, [C.c_uint64, _i32, _P(_i32), _P(_i32), _i32, _i64, _vp]),
     "zoom_dict_destroy": (None, [_vp]),
     "zoom_dict_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "zoom_dict_info": (C.c_int, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(C.c_double), _P(_i32), _P(_i32)]),

@@ -210,9 +210,9 @@ void zoom_ctx_destroy(zoom_ctx c) {
 zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
                                   const int32_t* heights, const int32_t* widths,
                                   int32_t n_images, const zoom_degradation* degr,
-                                  int64_t n_pairs, const int32_t* positions, void* stream,
+                                  int64_t n_pairs, const int32_t* positions, uint64_t seed, void* stream,
                                   zoom_dict* out) {
-  if (!ctx || !hr_images || !heights || !widths || !degr || !positions || !out)
+  if (!ctx || !hr_images || !heights || !widths || !degr || !out)
     return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
   const int s = degr->scale, P = degr->lr_patch;
   if (s < 1 || s > 4) return fail(ZOOM_ERR_INVALID_ARG, "scale must be in 1..4");
@@ -225,6 +225,21 @@ zoom_status zoom_build_dictionary(zoom_ctx ctx, const float* const* hr_images,
     if (!hr_images[m]) return fail(ZOOM_ERR_INVALID_ARG, "NULL image pointer");
     if (heights[m] / s < P || widths[m] / s < P)
       return fail(ZOOM_ERR_INVALID_ARG, "training image smaller than one patch");
+  }
+  // no positions given: draw them from the seed (uniform without
+  // replacement over the LR patch origins, in origin order)
+  std::vector<int32_t> drawn;
+  if (!positions) {
+    std::vector<int32_t> lh(n_images), lw(n_images);
+    for (int m = 0; m < n_images; ++m) {
+      lh[m] = heights[m] / s;
+      lw[m] = widths[m] / s;
+    }
+    if (n_pairs > zoom_count_origins(n_images, lh.data(), lw.data(), P))
+      return fail(ZOOM_ERR_INVALID_ARG, "n_pairs exceeds the LR patch origins of the images");
+    drawn.resize((size_t)n_pairs * 3);
+    zoom_sample_positions_host(seed, n_images, lh.data(), lw.data(), P, n_pairs, drawn.data());
+    positions = drawn.data();
   }
   for (int64_t e = 0; e < n_pairs; ++e) {
     int m = positions[3 * e], i = positions[3 * e + 1], j = positions[3 * e + 2];
@@ -338,6 +353,8 @@ zoom_status zoom_index_info(zoom_index ix, zoom_lsh_params* lsh) {
     lsh->w = ix->w;
     lsh->min_table_hits = ix->t;
     lsh->max_candidates = ix->cap;
+    lsh->proj_dist = ix->proj_dist;
+    lsh->seed = ix->seed;
   }
   return ZOOM_OK;
 }
@@ -362,7 +379,9 @@ zoom_status zoom_dict_export(zoom_dict d, float* lr_pix, float* mu, float* hr_re
 
 zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const float* alpha,
                              const float* beta, void* stream, zoom_index* out) {
-  if (!d || !lsh || !alpha || !beta || !out) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  if (!d || !lsh || !out) return fail(ZOOM_ERR_INVALID_ARG, "NULL argument");
+  if (!alpha != !beta) return fail(ZOOM_ERR_INVALID_ARG, "give both alpha and beta, or neither");
+  if (lsh->proj_dist < 0 || lsh->proj_dist > 1) return fail(ZOOM_ERR_INVALID_ARG, "proj_dist must be 0 or 1");
   if (lsh->L < 1 || lsh->L > 32 || lsh->k < 1 || lsh->k > 32)
     return fail(ZOOM_ERR_INVALID_ARG, "L and k must be in 1..32");
   if (!(lsh->w > 0.f) || !isfinite(lsh->w)) return fail(ZOOM_ERR_INVALID_ARG, "w must be > 0");
@@ -377,6 +396,15 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ZCHECK_CUDA(cudaSetDevice(ctx->device));
   const int64_t N = d->n;
   const int L = lsh->L, k = lsh->k;
+  // no draws given: the library's own, from the seed (zoom_lsh_draws)
+  std::vector<float> drawn_a, drawn_b;
+  if (!alpha) {
+    drawn_a.resize((size_t)L * k * d->d);
+    drawn_b.resize((size_t)L * k);
+    zoom_draw_projections(L, k, d->d, lsh->w, lsh->proj_dist, lsh->seed, drawn_a.data(), drawn_b.data());
+    alpha = drawn_a.data();
+    beta = drawn_b.data();
+  }
   zoom_index ix = new zoom_index_s();
   ix->dict = d;
   ix->L = L;
@@ -384,6 +412,8 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->w = lsh->w;
   ix->t = lsh->min_table_hits;
   ix->cap = lsh->max_candidates;
+  ix->proj_dist = drawn_a.empty() ? 0 : lsh->proj_dist;
+  ix->seed = drawn_a.empty() ? 0 : lsh->seed;
   ix->nd_rows = tc_rows_padded(N, false);
   {
     Carver c(nullptr);

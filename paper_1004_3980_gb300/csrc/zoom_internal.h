@@ -69,6 +69,8 @@ struct zoom_index_s {
   zoom_dict dict = nullptr;
   int L = 0, k = 0, t = 1, cap = 0;
   float w = 0.f;
+  int proj_dist = 0;         // the draws' law and seed when the library drew them
+  uint64_t seed = 0;
   float* alpha = nullptr;    // [L*k][d]
   float* beta = nullptr;     // [L*k]
   uint64_t* dkeys = nullptr; // [N][L]
@@ -89,6 +91,14 @@ struct zoom_index_s {
 // ---------------------------------------------------------------------------
 
 void zoom_set_error(const std::string& msg);
+
+// seeded draws (zoom_random.cu): the projections of Eq. 10 (dist 0
+// Gaussian, 1 Cauchy by Eq. 11) and the dictionary positions
+constexpr double kCauchyEps = 1e-3;
+void zoom_draw_projections(int L, int k, int D, float w, int dist, uint64_t seed, float* alpha, float* beta);
+int64_t zoom_count_origins(int n_images, const int32_t* lr_h, const int32_t* lr_w, int P);
+bool zoom_sample_positions_host(uint64_t seed, int n_images, const int32_t* lr_h, const int32_t* lr_w, int P,
+                                int64_t n_pairs, int32_t* positions);
 // A dictionary handle of n pairs with its (uninitialised) device arrays in
 // one allocation based at lr_pix; nullptr when the allocation fails.
 zoom_dict zoom_dict_alloc(zoom_ctx ctx, int64_t n, int P, int s, double blur_sigma, int feature,

@@ -142,21 +142,30 @@ class Dictionary:
     """LR/HR patch-pair dictionary built on the device (zoom_build_dictionary)."""
 
     def __init__(self, ctx: Context, hr_images, positions, scale: int, patch: int,
-                 blur_sigma: float = 0.8, stream=None, feature: int = 0):
-        """feature: 0 = LR pixels minus their mean, 1 = first-order gradients
-        of the LR image at the patch's pixels (Sec. 4.1)."""
+                 blur_sigma: float = 0.8, stream=None, feature: int = 0, n_pairs: int | None = None,
+                 seed: int = 7):
+        """feature: 0 = LR pixels minus their mean, 1 / 2 = first / second-
+        order gradients of the LR image at the patch's pixels (Sec. 4.1).
+        positions: int32 [n][3] (image, LR row, LR col), or None to let the
+        library draw n_pairs of them from `seed` (zoom_sample_positions)."""
         self.ctx = ctx
         for t in hr_images:
             _need(t, torch.float32, "hr image")
-        pos = np.ascontiguousarray(positions, dtype=np.int32)
         n = len(hr_images)
         ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hr_images])
         hs = (C.c_int32 * n)(*[t.shape[0] for t in hr_images])
         ws = (C.c_int32 * n)(*[t.shape[1] for t in hr_images])
         degr = capi.Degradation(scale, patch, blur_sigma, feature)
         h = C.c_void_p()
-        capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), len(pos),
-                  pos.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream), C.byref(h))
+        if positions is None:
+            if n_pairs is None:
+                raise ValueError("n_pairs is needed when the library draws the positions")
+            npos, pptr = int(n_pairs), None
+        else:
+            pos = np.ascontiguousarray(positions, dtype=np.int32)
+            npos, pptr = len(pos), pos.ctypes.data_as(C.POINTER(C.c_int32))
+        capi.call("zoom_build_dictionary", ctx.handle, ptrs, hs, ws, n, C.byref(degr), npos, pptr, int(seed),
+                  _stream(stream), C.byref(h))
         self._adopt(h)
 
     def _adopt(self, h):
@@ -234,17 +243,24 @@ def sample_crops(ctx: Context, images, u, crop_h: int, crop_w: int, want_crops: 
 class Index:
     """L-table p-stable LSH index over a dictionary (zoom_build_index)."""
 
-    def __init__(self, dictionary: Dictionary, L: int, k: int, w: float, alpha, beta,
-                 min_table_hits: int = 1, max_candidates: int = 0, stream=None):
+    def __init__(self, dictionary: Dictionary, L: int, k: int, w: float, alpha=None, beta=None,
+                 min_table_hits: int = 1, max_candidates: int = 0, stream=None, proj_dist: int = 0,
+                 seed: int = 11):
+        """alpha float32 [L*k][D], beta float32 [L*k] (Eq. 10), or both None
+        to let the library draw them from `seed` (proj_dist 0 Gaussian, 1
+        Cauchy by Eq. 11; zoom_lsh_draws)."""
         self.dictionary = dictionary
-        a = np.ascontiguousarray(alpha, np.float32)
-        b = np.ascontiguousarray(beta, np.float32)
-        if a.shape != (L * k, dictionary.dim) or b.shape != (L * k,):
-            raise ValueError(f"alpha must be [{L * k}][{dictionary.dim}] and beta [{L * k}]")
-        prm = capi.LshParams(L, k, w, min_table_hits, max_candidates)
+        prm = capi.LshParams(L, k, w, min_table_hits, max_candidates, proj_dist, int(seed))
+        if alpha is None and beta is None:
+            a = b = None
+        else:
+            a = np.ascontiguousarray(alpha, np.float32)
+            b = np.ascontiguousarray(beta, np.float32)
+            if a.shape != (L * k, dictionary.dim) or b.shape != (L * k,):
+                raise ValueError(f"alpha must be [{L * k}][{dictionary.dim}] and beta [{L * k}]")
         h = C.c_void_p()
-        capi.call("zoom_build_index", dictionary.handle, C.byref(prm), a.ctypes.data, b.ctypes.data,
-                  _stream(stream), C.byref(h))
+        capi.call("zoom_build_index", dictionary.handle, C.byref(prm), None if a is None else a.ctypes.data,
+                  None if b is None else b.ctypes.data, _stream(stream), C.byref(h))
         self._adopt(h)
 
     def _adopt(self, h):
@@ -469,6 +485,32 @@ def map_energy_grads(index: Index, lr: torch.Tensor, nbr: torch.Tensor, wgt: tor
     capi.call("zoom_backward", index.handle, _ptr(lr), h, w, _ptr(nbr), _ptr(wgt), nbr.shape[1], reg_rel, lam,
               _ptr(gx), _ptr(gd), ph2, _ptr(x), C.byref(e), _stream(stream))
     return {"energy": e.value, "grad_x": gx, "grad_dict": gd, "hr": x}
+
+
+# ---------------------------------------------------------------------------
+# seeded draws (host; the library's generator)
+# ---------------------------------------------------------------------------
+
+
+def lsh_draws(L: int, k: int, dim: int, w: float, seed: int, proj_dist: int = 0):
+    """The projections and offsets zoom_build_index draws from a seed
+    (zoom_lsh_draws): alpha float32 [L*k][dim], beta float32 [L*k]."""
+    prm = capi.LshParams(L, k, w, 1, 0, proj_dist, int(seed))
+    a = np.empty((L * k, dim), np.float32)
+    b = np.empty(L * k, np.float32)
+    capi.call("zoom_lsh_draws", C.byref(prm), dim, a.ctypes.data, b.ctypes.data)
+    return a, b
+
+
+def sample_positions(seed: int, lr_sizes, patch: int, n_pairs: int) -> np.ndarray:
+    """Dictionary positions drawn from a seed (zoom_sample_positions): int32
+    [n_pairs][3] (image, LR row, LR col) over the LR images of lr_sizes."""
+    n = len(lr_sizes)
+    hs = (C.c_int32 * n)(*[int(h) for h, _ in lr_sizes])
+    ws = (C.c_int32 * n)(*[int(w) for _, w in lr_sizes])
+    out = np.empty((n_pairs, 3), np.int32)
+    capi.call("zoom_sample_positions", int(seed), n, hs, ws, patch, n_pairs, out.ctypes.data)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -12,6 +12,7 @@ from tests import test_oracle_dictionary as TDI
 from tests import test_oracle_features as TF
 from tests import test_oracle_hash as TH
 from tests import test_oracle_knn_lle as TK
+from tests import test_oracle_random as TRN
 from tests import test_oracle_recon_bp as TR
 from tests import test_oracle_sampling as TS
 
@@ -222,3 +223,24 @@ def _dictionary_variant(hr_origin):
 def test_hr_cut_mistakes_are_caught(monkeypatch, origin):
     monkeypatch.setattr(O, "build_dictionary", _dictionary_variant(origin))
     _fails(TDI.test_dictionary_entries_of_a_ramp_have_closed_forms, 2, 5)
+
+
+@pytest.mark.parametrize("mistake", ["bump_first", "swap_hilo", "one_multiplier"])
+def test_philox_mistakes_are_caught(monkeypatch, mistake):
+    # the key bumped before the first round too, the high and low product
+    # words swapped, one multiplier for both lanes
+    def philox_bad(ctr, seed):
+        c = [int(x) for x in np.asarray(ctr, np.uint64).reshape(-1, 4)[0]]
+        k0, k1 = seed & 0xFFFFFFFF, seed >> 32
+        m0, m1 = O.PHILOX_M if mistake != "one_multiplier" else (O.PHILOX_M[0],) * 2
+        for r in range(10):
+            if r > 0 or mistake == "bump_first":
+                k0, k1 = (k0 + O.PHILOX_W[0]) & 0xFFFFFFFF, (k1 + O.PHILOX_W[1]) & 0xFFFFFFFF
+            p0, p1 = m0 * c[0], m1 * c[2]
+            hi0, lo0, hi1, lo1 = p0 >> 32, p0 & 0xFFFFFFFF, p1 >> 32, p1 & 0xFFFFFFFF
+            if mistake == "swap_hilo":
+                hi0, lo0, hi1, lo1 = lo0, hi0, lo1, hi1
+            c = [(hi1 ^ c[1] ^ k0) & 0xFFFFFFFF, lo1, (hi0 ^ c[3] ^ k1) & 0xFFFFFFFF, lo0]
+        return np.array([c], np.uint32)
+    monkeypatch.setattr(O, "philox4x32_10", philox_bad)
+    _fails(TRN.test_philox_known_answers, *TRN.KAT[2])
