@@ -697,6 +697,296 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The wide-step filter for the narrow operands (single FP16 term or BF16,
+// K = 32 or 64): each query tile's MMA is M = 128 x N = 256 (two 128-row
+// dictionary tiles in one 256-row step), one 256-column accumulator per
+// query tile (the two fill the TMEM), so an issuing thread spends half the
+// instructions and commits of the 128 x 128 form per unit of work and, while
+// the epilogue reads one query tile's accumulator, the tensor pipe computes
+// the other's.
+//   warp 0      producer: the item's two query tiles, then 256-row steps of
+//               the dictionary (one bulk copy each) into a ring
+//   warps 1, 10 issue the MMAs of query tile 0 and 1
+//   warps 2..9  epilogue: warps 2..5 read query tile 0's accumulator (one
+//               warp per TMEM lane quadrant), warps 6..9 tile 1's; each reads
+//               its 32 rows x 256 columns per step in two rounds of four
+//               32-column loads, testing the first round's chunk minima while
+//               the second round's loads are in flight
+// Chunk c of step t is entries 256 t + 32 c .. +31 (columns 32 c .. 32 c + 31).
+// ---------------------------------------------------------------------------
+constexpr int TW_ROWS = 256;              // dictionary rows per step (MMA N)
+__host__ __device__ constexpr int tw_epi_bytes(int MC) { return 16 * 256 * 8 + MC * 256 * 8; }
+__host__ __device__ constexpr int tw_stages(int KC, int MC) {
+  return (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16) < 12
+             ? (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16)
+             : 12;
+}
+static_assert(tw_stages(4, 16) == 9 && tw_stages(4, 32) == 7 && tw_stages(8, 16) == 4 && tw_stages(8, 32) == 3,
+              "wide ring depths");
+// kind::f16, D fp32, A and B of one type, K-major, M = 128, N = 256.
+__host__ __device__ constexpr uint32_t instr_desc_wide(uint32_t ab_type) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(TW_ROWS >> 3) << 17) |
+         ((uint32_t)(TC_ROWS >> 4) << 24);
+}
+
+template <int KC, int MC, uint32_t AB_TYPE>
+__global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
+  constexpr uint32_t kATile = KC * TC_ROWS * 16;     // one 128-row query tile
+  constexpr uint32_t kStep = KC * TW_ROWS * 16;      // one 256-row dictionary step
+  constexpr int kKSteps = KC / 2;
+  constexpr uint32_t kIdesc = instr_desc_wide(AB_TYPE);
+  constexpr int kStages = tw_stages(KC, MC);
+  constexpr int kBufW = 16;                          // append slots per epilogue lane
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;                          // 2 query tiles
+  unsigned char* sB = smem + 2 * kATile;             // kStages dictionary steps
+  uint64_t* bars = (uint64_t*)(sB + kStages * kStep);
+  uint64_t* a_full = bars + 0;
+  uint64_t* a_empty = bars + 1;
+  uint64_t* b_full = bars + 2;                 // [kStages]
+  uint64_t* b_empty = b_full + kStages;        // [kStages]
+  uint64_t* acc_full = b_empty + kStages;      // [2] per query tile
+  uint64_t* acc_empty = acc_full + 2;          // [2]
+  uint64_t* drain = acc_empty + 2;             // [2] one per issuing thread, at exit
+  uint32_t* tmem_slot = (uint32_t*)(drain + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBufW][256]
+  int* buf_i = (int*)(buf_v + kBufW * 256);                      // [kBufW][256]
+  float* lst_v = (float*)(buf_i + kBufW * 256);                  // [MC][256]
+  int* lst_i = (int*)(lst_v + MC * 256);                         // [MC][256]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    mbar_init(a_empty, 2);   // one commit per issuing thread
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(b_full + s, 1);
+      mbar_init(b_empty + s, 2);   // one release per query tile
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(acc_full + q, 1);
+      mbar_init(acc_empty + q, 4);   // the query tile's four epilogue warps
+      mbar_init(drain + q, 1);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, a_phase = 0;
+      bool first = true;
+      int a_copies = 0;
+      int64_t b_copies = 0;
+      WorkIter it;
+      int qp, seg, t0, t1;
+      while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
+        if (!first) {
+          if (!mbar_wait(a_empty, a_phase, abort_flag, a.status, a.wait_ns)) break;
+          a_phase ^= 1u;
+        }
+        first = false;
+        mbar_arrive_expect_tx(a_full, 2 * kATile);
+        bulk_g2s(sA, (const unsigned char*)a.qop + (size_t)qp * 2 * kATile, 2 * kATile, a_full);
+        ++a_copies;
+        for (int t = t0; t < t1; ++t) {
+          if (!mbar_wait_fast(b_empty + stage, phase ^ 1u, abort_flag, a.status, a.wait_ns)) break;
+          mbar_arrive_expect_tx(b_full + stage, kStep);
+          bulk_g2s(sB + stage * kStep, (const unsigned char*)a.dop + (size_t)t * kStep, kStep, b_full + stage);
+          ++b_copies;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (a_copies > 0) mbar_drain(a_full, (uint32_t)(a_copies - 1) & 1u, a.status);
+      for (int64_t i = b_copies - kStages > 0 ? b_copies - kStages : 0; i < b_copies; ++i)
+        mbar_drain(b_full + i % kStages, (uint32_t)(i / kStages) & 1u, a.status);
+    }
+  } else if (warp == 1 || warp == 10) {
+    // ---------------- MMA issue: one thread per query tile ----------------
+    if (lane == 0) {
+      const int qt = warp == 1 ? 0 : 1;
+      int stage = 0, items = 0;
+      uint32_t phase = 0, a_phase = 0, accp = 0;
+      // query tile: K-major, core matrices 8 rows x 16 B, K chunks 128 rows
+      // apart; dictionary step: the same with 256 rows (LBO 4 KiB)
+      const uint64_t ad0 = smem_desc(smem_u32(sA + qt * kATile), TC_ROWS * 16, 128);
+      const uint64_t bd0 = smem_desc(smem_u32(sB), TW_ROWS * 16, 128);
+      constexpr uint64_t kAStep = (2 * TC_ROWS * 16) >> 4;
+      constexpr uint64_t kBStep = (2 * TW_ROWS * 16) >> 4;
+      constexpr uint64_t kStageAdv = kStep >> 4;
+      const uint32_t d_addr = tmem + (uint32_t)(qt * TW_ROWS);
+      WorkIter it;
+      int qp, seg, t0, t1;
+      while (!*abort_flag && it.next(a, qp, seg, t0, t1)) {
+        if (!mbar_wait_fast(a_full, a_phase, abort_flag, a.status, a.wait_ns)) break;
+        a_phase ^= 1u;
+        tc_fence_after();
+        bool ok = true;
+        for (int t = t0; t < t1; ++t) {
+          if (!mbar_wait_fast(b_full + stage, phase, abort_flag, a.status, a.wait_ns) ||
+              !mbar_wait_fast(acc_empty + qt, accp ^ 1u, abort_flag, a.status, a.wait_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t bd_s = bd0 + (uint64_t)stage * kStageAdv;
+#pragma unroll
+          for (int ks = 0; ks < kKSteps; ++ks)
+            mma_f16(d_addr, ad0 + ks * kAStep, bd_s + ks * kBStep, kIdesc, ks > 0 ? 1u : 0u);
+          mma_commit(acc_full + qt);   // also frees the ring stage (the epilogue releases it)
+          accp ^= 1u;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        mma_commit(a_empty);
+        ++items;
+        if (!ok) break;
+      }
+      if (items > 0) mbar_drain(a_empty, (uint32_t)(items - 1) & 1u, a.status);
+      mma_commit(drain + qt);
+      mbar_drain(drain + qt, 0u, a.status);
+    }
+  } else {
+    // ------------- epilogue: per query, the MC best 32-entry chunks -------------
+    const int ew = warp - 2;            // 0..7
+    const int qt = ew >> 2;             // query tile
+    const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;
+    float* bv = buf_v + ew * 32 + lane;
+    int* bi = buf_i + ew * 32 + lane;
+    float* sl_v = lst_v + ew * 32 + lane;
+    int* sl_i = lst_i + ew * 32 + lane;
+    const bool releaser = quad == 0 && lane == 0;   // frees each step's ring stage (one per query tile)
+    int stage = 0, item_no = 0;
+    uint32_t accp = 0;
+    WorkIter it;
+    int qp, split, t0, t1;
+    while (it.next(a, qp, split, t0, t1)) {
+      if (__any_sync(kFull, *abort_flag != 0)) break;   // warp-uniform exit
+      const bool withhold = a.inject == 1 && item_no++ == 0;   // testing aid (see TcArgs)
+      const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
+      const bool valid = q < a.nq;
+      const float qn = valid ? a.qn[q] : 0.f;
+      float ld[MC];
+      int li[MC];
+#pragma unroll
+      for (int j = 0; j < MC; ++j) {
+        ld[j] = FLT_MAX;
+        li[j] = -1;
+        sl_v[j * 256] = FLT_MAX;
+        sl_i[j * 256] = -1;
+      }
+      float thr = FLT_MAX;
+      int cnt = 0;
+      auto flush = [&]() {
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+          ld[j] = sl_v[j * 256];
+          li[j] = sl_i[j * 256];
+        }
+        flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+          sl_v[j * 256] = ld[j];
+          sl_i[j * 256] = li[j];
+        }
+      };
+      bool ok = true;
+      for (int t = t0; t < t1; ++t) {
+        const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + qt, accp, abort_flag, a.status, a.wait_ns));
+        if (!w) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (releaser) mbar_arrive(b_empty + stage);   // the MMAs that read the stage are done
+        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(qt * TW_ROWS);
+        float va[32], vb[32], vc[32], vd[32], m0, m1, m2, m3, m4, m5, m6, m7;
+        tmem_ld32_min_issue(tb, va, m0);
+        tmem_ld32_min_issue(tb + 32, vb, m1);
+        tmem_ld32_min_issue(tb + 64, vc, m2);
+        tmem_ld32_min_issue(tb + 96, vd, m3);
+        tmem_ld_wait(va, m0);
+        tmem_regs_ready(vb, m1);
+        tmem_regs_ready(vc, m2);
+        tmem_regs_ready(vd, m3);
+        // the second half's loads run while the first half's chunks are tested
+        tmem_ld32_min_issue(tb + 128, va, m4);
+        tmem_ld32_min_issue(tb + 160, vb, m5);
+        tmem_ld32_min_issue(tb + 192, vc, m6);
+        tmem_ld32_min_issue(tb + 224, vd, m7);
+        const int c0 = t * 8;
+        chunk_test(m0, c0, thr, bv, bi, cnt);
+        chunk_test(m1, c0 + 1, thr, bv, bi, cnt);
+        chunk_test(m2, c0 + 2, thr, bv, bi, cnt);
+        chunk_test(m3, c0 + 3, thr, bv, bi, cnt);
+        tmem_ld_wait(va, m4);
+        tmem_regs_ready(vb, m5);
+        tmem_regs_ready(vc, m6);
+        tmem_regs_ready(vd, m7);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0 && (!withhold || t < t0 + 2)) mbar_arrive(acc_empty + qt);   // every read of it is done
+        chunk_test(m4, c0 + 4, thr, bv, bi, cnt);
+        chunk_test(m5, c0 + 5, thr, bv, bi, cnt);
+        chunk_test(m6, c0 + 6, thr, bv, bi, cnt);
+        chunk_test(m7, c0 + 7, thr, bv, bi, cnt);
+        accp ^= 1u;
+        if (++stage == kStages) stage = 0;
+        // room for the next step's up to 8 appends in every lane
+        if (__any_sync(kFull, cnt > kBufW - 8)) flush();
+      }
+      if (!ok) break;
+      flush();
+      if (valid) {
+        float* od = a.out_d + ((int64_t)split * a.nq + q) * MC;
+        int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+          const bool real = li[j] >= 0 && (int64_t)li[j] * 32 < a.nd;
+          od[j] = real ? qn + ld[j] : FLT_MAX;
+          oi[j] = real ? li[j] : -1;
+        }
+        if (a.tail_split > 0 && t0 == 0 && t1 == a.nd_tiles) {
+          for (int s2 = 1; s2 < a.tail_split; ++s2) {
+            float* od1 = a.out_d + ((int64_t)s2 * a.nq + q) * MC;
+            int32_t* oi1 = a.out_id + ((int64_t)s2 * a.nq + q) * MC;
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+              od1[j] = FLT_MAX;
+              oi1[j] = -1;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // operand preparation
 // ---------------------------------------------------------------------------
 
@@ -705,6 +995,11 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
 __device__ __forceinline__ int64_t op_off(int64_t r, int k, int KC) {
   return (r / TC_ROWS) * ((int64_t)KC * TC_ROWS * 8) + (int64_t)(k >> 3) * (TC_ROWS * 8) +
          (r % TC_ROWS) * 8 + (k & 7);
+}
+// The same layout with tiles of `rows` rows ([tile][kc][rows][8]): the
+// dictionary operands of the wide-step filter use 256-row tiles.
+__device__ __forceinline__ int64_t op_off_rows(int64_t r, int k, int KC, int rows) {
+  return (r / rows) * ((int64_t)KC * rows * 8) + (int64_t)(k >> 3) * (rows * 8) + (r % rows) * 8 + (k & 7);
 }
 
 __device__ __forceinline__ uint16_t h_bits(__half h) { return __half_as_ushort(h); }
@@ -809,7 +1104,7 @@ __global__ void k_operand_bf16(const float* __restrict__ feat, int dpad, int64_t
     pk.y = (uint32_t)row[kc * 8 + 2] | ((uint32_t)row[kc * 8 + 3] << 16);
     pk.z = (uint32_t)row[kc * 8 + 4] | ((uint32_t)row[kc * 8 + 5] << 16);
     pk.w = (uint32_t)row[kc * 8 + 6] | ((uint32_t)row[kc * 8 + 7] << 16);
-    *reinterpret_cast<uint4*>(op + op_off(r, kc * 8, KC)) = pk;
+    *reinterpret_cast<uint4*>(op + op_off_rows(r, kc * 8, KC, role == 1 ? 256 : TC_ROWS)) = pk;
   }
 }
 
@@ -858,7 +1153,7 @@ __global__ void k_operand_f16s(const float* __restrict__ feat, int dpad, int64_t
     pk.y = (uint32_t)row[kc * 8 + 2] | ((uint32_t)row[kc * 8 + 3] << 16);
     pk.z = (uint32_t)row[kc * 8 + 4] | ((uint32_t)row[kc * 8 + 5] << 16);
     pk.w = (uint32_t)row[kc * 8 + 6] | ((uint32_t)row[kc * 8 + 7] << 16);
-    *reinterpret_cast<uint4*>(op + op_off(r, kc * 8, KC)) = pk;
+    *reinterpret_cast<uint4*>(op + op_off_rows(r, kc * 8, KC, role == 1 ? 256 : TC_ROWS)) = pk;
   }
 }
 
@@ -990,11 +1285,17 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
   float lv[kMaxSplit];
   int lcv[kMaxSplit], hd[kMaxSplit];
 #pragma unroll
+  // An entry naming no chunk of the dictionary counts as "none" (FLT_MAX):
+  // the filter writes only real chunks or (FLT_MAX, -1), but a filter that
+  // gave up (a wait ran out) leaves its lists unwritten, and their contents
+  // must not become addresses.
   for (int s = 0; s < kMaxSplit; ++s) {
     const bool has = s < nsplit && lane < MC;
     const int64_t o = ((int64_t)s * nq + q) * MC + lane;
-    lv[s] = has ? lm[o] : FLT_MAX;
-    lcv[s] = has ? lc[o] : 0;
+    const int c = has ? lc[o] : -1;
+    const bool real = c >= 0 && (int64_t)c * 32 < nd;
+    lv[s] = real ? lm[o] : FLT_MAX;
+    lcv[s] = real ? c : -1;
     hd[s] = 0;
   }
   // T: the smallest list threshold (MC-th listed minimum) over the splits
@@ -1031,7 +1332,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
   auto stage = [&](int c, int b) {
     if (c >= 0) {
       const int64_t e0 = (int64_t)c * 32;
-      const int nrows = nd - e0 < 32 ? (int)(nd - e0) : 32;
+      const int nrows = (int)(nd - e0 < 32 ? nd - e0 : 32);
       const float4* g = reinterpret_cast<const float4*>(dfeat + e0 * kDP);
       float4* dst = s_rows[wib][b];
       for (int f = lane; f < nrows * kRow4; f += 32) cp_async16(dst + f, g + f);
@@ -1063,7 +1364,7 @@ __global__ __launch_bounds__(rerank_warps(D) * 32, D > 32 ? 8 : 7) void k_rerank
     __syncwarp();         // ... and every lane's
     const int64_t e0 = (int64_t)chunk * 32;
     const int64_t e = e0 + lane;
-    const int nrows = nd - e0 < 32 ? (int)(nd - e0) : 32;
+    const int nrows = (int)(nd - e0 < 32 ? nd - e0 : 32);
     float dd = FLT_MAX;
     if (lane < nrows) {
       const float4* srow = s_rows[wib][buf];
@@ -1251,6 +1552,26 @@ int tc_list_size(int precision, int K, int rerank_mult) {
   return rerank_mult * K <= 16 ? 16 : 32;
 }
 
+size_t tw_smem_bytes(int KC, int MC) {
+  return 1024 + (size_t)2 * KC * TC_ROWS * 16 + (size_t)tw_stages(KC, MC) * KC * TW_ROWS * 16 + kBarBytes +
+         (size_t)tw_epi_bytes(MC);
+}
+
+bool tc_wide_form(int precision, int kc) { return precision != 0 && (kc == 4 || kc == 8); }
+
+template <int KC, int MC, uint32_t T>
+static cudaError_t run_tw_kernel(const TcArgs& args, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_knn_tw<KC, MC, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (fa.maxThreadsPerBlock < 352) return cudaErrorLaunchOutOfResources;
+  kern<<<grid, 352, smem, st>>>(args);
+  return cudaGetLastError();
+}
+
 template <int KC, int MC, uint32_t T>
 static cudaError_t run_tc_kernel(const TcArgs& args, int grid, size_t smem, cudaStream_t st) {
   auto kern = k_knn_tc<KC, MC, T>;
@@ -1270,6 +1591,40 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
                           int64_t nd, int precision, int kc, int MC, int nsplit, int tail_split, int grid,
                           float* out_d, int32_t* out_id, unsigned int* status, cudaStream_t st,
                           const unsigned long long* nq_dev, uint64_t wait_ns, int inject) {
+  if (tc_wide_form(precision, kc)) {
+    // the wide-step kernel: items of 256 queries x a part of the 256-row steps
+    if (nq_dev || (MC != 16 && MC != 32)) return cudaErrorInvalidValue;
+    TcArgs a;
+    a.wait_ns = wait_ns > 0 ? wait_ns : kWaitNs;
+    a.inject = inject;
+    a.qop = qop;
+    a.qn = qn;
+    a.dop = dop;
+    a.nq = nq;
+    a.nq_dev = nullptr;
+    a.nd = nd;
+    a.nq_pairs = (int)((nq + 2 * TC_ROWS - 1) / (2 * TC_ROWS));
+    a.nd_tiles = (int)((nd + TW_ROWS - 1) / TW_ROWS);   // 256-row steps
+    a.nsplit = nsplit;
+    a.tiles_per_split = (a.nd_tiles + nsplit - 1) / nsplit;
+    a.out_d = out_d;
+    a.out_id = out_id;
+    a.status = status;
+    a.tail_split = tail_split;
+    if (tail_split > 0 && nsplit != tail_split) return cudaErrorInvalidValue;
+    const int items = tail_split > 0 ? a.nq_pairs : a.nsplit * a.nq_pairs;
+    grid = grid < items ? grid : items;
+    a.full_rounds = tail_split > 0 ? a.nq_pairs / grid : 0;
+    const size_t smem = tw_smem_bytes(kc, MC);
+#define ZOOM_TW(KC, T) \
+  return MC == 16 ? run_tw_kernel<KC, 16, T>(a, grid, smem, st) : run_tw_kernel<KC, 32, T>(a, grid, smem, st)
+    if (precision == 2 && kc == 4) ZOOM_TW(4, 0);
+    if (precision == 2 && kc == 8) ZOOM_TW(8, 0);
+    if (precision == 1 && kc == 4) ZOOM_TW(4, 1);
+    if (precision == 1 && kc == 8) ZOOM_TW(8, 1);
+#undef ZOOM_TW
+    return cudaErrorInvalidValue;
+  }
   TcArgs a;
   a.wait_ns = wait_ns > 0 ? wait_ns : kWaitNs;
   a.inject = inject;

@@ -414,7 +414,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
   ix->cap = lsh->max_candidates;
   ix->proj_dist = drawn_a.empty() ? 0 : lsh->proj_dist;
   ix->seed = drawn_a.empty() ? 0 : lsh->seed;
-  ix->nd_rows = tc_rows_padded(N, false);
+  ix->nd_rows = tc_rows_padded(N, true);   // whole 256-row steps for the wide-step filter
   {
     Carver c(nullptr);
     c.take<float>((size_t)L * k * d->d);
@@ -546,7 +546,10 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   // stage (internal precision 2), or the split filter alone (search 3)
   p.prec = prm->precision == 1 ? 1 : (prm->search == 3 ? 0 : 2);
   p.MC = mc_override > 0 ? mc_override : tc_list_size(p.prec, prm->K, prm->rerank_mult);
-  const int64_t nd_tiles = ix->nd_rows / 128;
+  p.KCH = tc_kc(d->d, p.prec) * 8;
+  // the narrow forms step through the dictionary 256 rows at a time
+  const int64_t unit_rows = tc_wide_form(p.prec, p.KCH / 8) ? 256 : 128;
+  const int64_t nd_tiles = ix->nd_rows / unit_rows;
   const int64_t nq_pairs = (nq + 255) / 256;
   // Every CTA streams the dictionary tiles in the same order at about the
   // same pace, so L2 serves nearly all of them whatever the dictionary size.
@@ -554,8 +557,8 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   // round decides the run time: the split count minimises the tiles of the
   // busiest CTA, each item charged a restart of its best chunk lists (about
   // MC*(1 + ln(N/32/MC)) merged chunks per query, most in the first tiles),
-  // measured at about kRestartTiles dictionary tiles.
-  constexpr int64_t kRestartTiles = 768;
+  // measured at about 768 128-row tiles (98,304 rows).
+  const int64_t kRestartTiles = 98304 / unit_rows;
   int64_t nsplit = nsplit_override;
   if (nsplit <= 0 && nq_pairs >= d->ctx->n_sm) {
     // whole pairs in step over all SMs (every CTA streams the dictionary from
@@ -592,7 +595,6 @@ SearchPlan plan_search(zoom_index ix, const zoom_upscale_params* prm, int64_t nq
   }
   p.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, std::min<int64_t>(8, nd_tiles)));
   p.q_rows = tc_rows_padded(nq, true);
-  p.KCH = tc_kc(d->d, p.prec) * 8;
   if (p.prec == 2) {
     // room for 4x the unsettled share measured on the 1M-pair workload
     // (0.4 %): queries past it go straight to the (slow) SIMT scan

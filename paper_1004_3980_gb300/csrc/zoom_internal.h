@@ -167,6 +167,11 @@ int tc_list_size(int precision, int K, int rerank_mult);
 // tail_split > 0: whole query pairs round robin for the full rounds over the
 // grid, the remaining pairs cut into tail_split dictionary parts (nsplit must
 // equal tail_split); 0: nsplit round-robin splits of every pair
+// The single-term FP16 and BF16 filters (precision 2 and 1, kc 4 or 8) run
+// as the wide-step kernel: 256-row dictionary steps, whose operand is laid
+// out in 256-row tiles ([tile][kc][256][8]); the dictionary operand needs
+// whole 256-row steps (an even number of 128-row tiles).
+bool tc_wide_form(int precision, int kc);
 // wait_ns: bound on every device wait (0: 2 s); inject: testing aid (1: the
 // epilogue withholds its accumulator releases, so a wait runs out)
 cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, const uint16_t* dop,

@@ -4,6 +4,9 @@
     sets: zoom_set_fault_injection) is reported as ZOOM_ERR_TIMEOUT by
     zoom_sync_status, and the next call on the same context gives the SIMT
     scan's neighbours again;
+  * the lists of a filter that gave up are never written; the rerank
+    reads them (random bytes, from an allocator that fills every block)
+    without following a chunk number outside the dictionary;
   * an allocation the context's allocator refuses makes the call return
     ZOOM_ERR_OOM with every allocation it made freed (the counts balance),
     except the blended-patch scratch of the overlap average, whose refusal
@@ -46,6 +49,25 @@ class CountingAllocator:
         torch.cuda.caching_allocator_delete(ptr)
 
 
+class GarbageAllocator:
+    """Device memory as PyTorch byte tensors filled with seeded random bytes:
+    whatever a kernel reads without having written it first is garbage, the
+    same garbage in every run."""
+
+    def __init__(self, seed: int = 5):
+        self.live = {}
+        self.gen = torch.Generator(device="cuda")
+        self.gen.manual_seed(seed)
+
+    def alloc(self, nbytes, stream, user):
+        t = torch.randint(0, 256, (int(nbytes),), dtype=torch.uint8, device="cuda", generator=self.gen)
+        self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(self, ptr, nbytes, stream, user):
+        self.live.pop(ptr)
+
+
 @pytest.fixture(scope="module")
 def small():
     from paper_1004_3980_gb300 import build
@@ -79,6 +101,37 @@ def test_filter_wait_timeout_is_reported_and_the_context_recovers(small, prm):
     else:
         hits = sum((r["nbr"] == ref["nbr"][:, m:m + 1]).any(dim=1).int() for m in range(wl.K))
         assert float(hits.double().mean()) / wl.K >= 0.99
+
+
+@pytest.mark.parametrize("prm", [dict(search=2), dict(precision=1, rerank_mult=2)], ids=["exact", "bf16"])
+def test_a_filter_that_gave_up_leaves_lists_the_rerank_never_follows(small, prm):
+    # The filter's waits run out before it writes any list, so the chunk
+    # lists the rerank reads are the random bytes of the scratch memory:
+    # chunk numbers outside the dictionary must count as "none" (never an
+    # address), and every neighbour returned is still a dictionary entry.
+    import paper_1004_3980_gb300 as Z
+    from paper_1004_3980_gb300.capi import ZoomError
+    case = small[0]
+    wl = case.wl
+    A = GarbageAllocator()
+    ctx, d, ix = G.gpu_build(case, Z.Context(0, allocator=A))
+    lr = torch.from_numpy(case.lr).cuda()
+    ref = Z.query(ix, lr, G.params(wl, search=1))
+    ctx.sync_status()
+    ctx.set_fault_injection(1, 20_000_000)
+    try:
+        r = Z.query(ix, lr, G.params(wl, **prm))
+        with pytest.raises(ZoomError, match="TIMEOUT"):
+            ctx.sync_status()
+    finally:
+        ctx.set_fault_injection(0, 0)
+    ctx.sync_status()
+    n = len(case.positions)
+    assert int(r["nbr"].min()) >= 0 and int(r["nbr"].max()) < n
+    r = Z.query(ix, lr, G.params(wl, **prm))
+    ctx.sync_status()
+    if prm.get("precision", 0) == 0:
+        assert torch.equal(r["nbr"], ref["nbr"]) and torch.equal(r["dist"], ref["dist"])
 
 
 def test_fault_injection_rejects_bad_arguments(small):
