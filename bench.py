@@ -594,15 +594,16 @@ def run_single(a, wl, config, rank, world, local):
                 "peak_source": peak_src + ", bf16 dense burst (fp16 runs at the bf16 rate)",
                 "sustained_peak": tc_sus}
 
-    rf_bf = filt_roofline("k_knn_tc<4,32,1> (tcgen05 BF16 distance filter, 32-chunk lists)",
+    rf_bf = filt_roofline("k_knn_tw<4,32,1,packed> (tcgen05 M128 x N256 BF16 distance filter, "
+                          "32-chunk packed lists)",
                           stage_bf.get("knn_filter_kernel", 0.0), 32, "one BF16 term, K = 32 per pair")
-    rf_ex = filt_roofline("k_knn_tc<4,16,0> (tcgen05 single-term FP16 filter of the exact form)",
+    rf_ex = filt_roofline("k_knn_tw<4,16,0> (tcgen05 M128 x N256 single-term FP16 filter of the exact form)",
                           stage_ex.get("knn_filter_kernel", 0.0), 32, "one FP16 term, K = 32 per pair")
     if rf_bf:
         rf_bf["traffic"] = profiled_traffic("paper_1004_3980_gb300/csrc/kernels_tc.cu",
-                                            "profiles/knn_tc_bf16_zoom3x_1920x1080_dict4m.md")
+                                            "profiles/knn_tw_bf16_zoom3x_1920x1080_dict4m.md")
         rf_bf["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
-                                   "(profiles/knn_tc_bf16_zoom3x_1920x1080_dict4m.md); null once the kernel "
+                                   "(profiles/knn_tw_bf16_zoom3x_1920x1080_dict4m.md); null once the kernel "
                                    "source differs from the captured one")
     PH2 = (wl.scale * wl.patch) ** 2
     oa_bytes = nq * wl.K * PH2 * 4 + hr_px * 4 + nq * (wl.K * 8 + 4)
@@ -703,7 +704,7 @@ def all_extras(a, wl, ctx, d, ix, lr, hr_exact, params, train, pos, st, world, h
         "value": world * hr_px / 1e6 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4,
         "feature_dim": D_g, "w": GRAD_W, "mean_bucket_sum_per_query": st_g["mean_bucket_sum"],
         "filter_fallback_queries": st_g["n_filter_fallback"],
-        "roofline": {"kernel": "k_knn_tc<8,16,0> (single-term FP16, K = 64)", "bound": "tensor",
+        "roofline": {"kernel": "k_knn_tw<8,16,0> (M128 x N256 single-term FP16, K = 64)", "bound": "tensor",
                      "achieved": ach_g, "peak": tc_peak, "unit": "TFLOP/s",
                      "frac": ach_g / tc_peak if ach_g else None, "kernel_ms": fg,
                      "work": f"{nq} queries x {wl.n_pairs} entries x 2 x 64 flops (dense)"}}

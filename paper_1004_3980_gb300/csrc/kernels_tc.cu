@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <float.h>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "zoom_internal.h"
@@ -325,6 +326,9 @@ struct TcArgs {
   // tile of its first item on, so the issuing threads' waits run out
   uint64_t wait_ns;
   int inject;
+  // packed chunk lists (the BF16 form of the wide-step filter): bits of a
+  // list key that hold the chunk number
+  int id_bits;
 };
 
 // Queries searched: nq, or the device count when one is given (read where
@@ -734,28 +738,171 @@ __global__ void __maxnreg__(tc_max_regs(KC, MC)) k_knn_tc(TcArgs a) {
 // Chunk c of step t is entries 256 t + 32 c .. +31 (columns 32 c .. 32 c + 31).
 // ---------------------------------------------------------------------------
 constexpr int TW_ROWS = 256;              // dictionary rows per step (MMA N)
-__host__ __device__ constexpr int tw_epi_bytes(int MC) { return 16 * 256 * 8 + MC * 256 * 8; }
-__host__ __device__ constexpr int tw_stages(int KC, int MC) {
-  return (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16) < 12
-             ? (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16)
+// append slots per epilogue lane ((value, index) pairs), and the lists:
+// (value, index) pairs, or 32-bit keys
+__host__ __device__ constexpr int tw_buf(bool) { return 16; }
+__host__ __device__ constexpr int tw_epi_bytes(int MC, bool packed) {
+  return tw_buf(packed) * 256 * 8 + MC * 256 * (packed ? 4 : 8);
+}
+__host__ __device__ constexpr int tw_stages(int KC, int MC, bool packed) {
+  return (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC, packed) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16) < 12
+             ? (kSmemMax - 1024 - kBarBytes - tw_epi_bytes(MC, packed) - 2 * KC * TC_ROWS * 16) / (KC * TW_ROWS * 16)
              : 12;
 }
-static_assert(tw_stages(4, 16) == 9 && tw_stages(4, 32) == 7 && tw_stages(8, 16) == 4 && tw_stages(8, 32) == 3,
+static_assert(tw_stages(4, 16, false) == 9 && tw_stages(4, 32, false) == 7 && tw_stages(8, 16, false) == 4 &&
+                  tw_stages(8, 32, false) == 3 && tw_stages(4, 16, true) == 10 && tw_stages(4, 32, true) == 9 &&
+                  tw_stages(8, 16, true) == 4 && tw_stages(8, 32, true) == 4,
               "wide ring depths");
+
+// The per-query list of the MC best chunks, kept by one epilogue lane: a
+// sorted list in shared memory (this lane's column, entry j at [j * 256]),
+// candidates appended to a shared-memory buffer and merged when some lane
+// of the warp runs out of room (the merge runs with the warp converged).
+// ChunkListF: FP32 minima d~ - ||q||^2 with chunk numbers, in two arrays.
+template <int MC, int BUFW>
+struct ChunkListF {
+  float* bv;
+  int* bi;
+  float* sv;
+  int* si;
+  float thr = FLT_MAX;
+  int cnt = 0;
+  __device__ void init() {
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      sv[j * 256] = FLT_MAX;
+      si[j * 256] = -1;
+    }
+    thr = FLT_MAX;
+    cnt = 0;
+  }
+  __device__ __forceinline__ void test(float m, int chunk) { chunk_test(m, chunk, thr, bv, bi, cnt); }
+  __device__ __forceinline__ bool full() const { return cnt > BUFW - 8; }
+  __device__ void flush() {
+    float ld[MC];
+    int li[MC];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      ld[j] = sv[j * 256];
+      li[j] = si[j * 256];
+    }
+    flush_appends<MC>(ld, li, thr, bv, bi, cnt);
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      sv[j * 256] = ld[j];
+      si[j * 256] = li[j];
+    }
+  }
+  // the list as chunk minima of d~ (FLT_MAX / -1: none)
+  __device__ void write(float qn, int64_t nd, float* od, int32_t* oi) const {
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      const float v = sv[j * 256];
+      const int c = si[j * 256];
+      const bool real = c >= 0 && (int64_t)c * 32 < nd;
+      od[j] = real ? qn + v : FLT_MAX;
+      oi[j] = real ? c : -1;
+    }
+  }
+};
+
+// Order-preserving map of FP32 values to 32-bit keys (a < b iff key(a) <
+// key(b)) and back.
+__device__ __forceinline__ uint32_t f32_order_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float f32_from_order_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// ChunkListK: the sorted list holds one 32-bit key per entry, the order
+// key of the chunk minimum d~ = ||q||^2 + (d~ - ||q||^2) with its low
+// id_bits replaced by the chunk number.  The replaced bits round d~ down (to
+// 32 - id_bits significant key bits: 6 mantissa bits for up to 2^17
+// chunks), so the listed value stays a lower bound of the chunk's entries,
+// which is all the rerank's stop rule needs; chunks closer than that are
+// ranked by number.  Merging into sorted keys takes two integer min/max per
+// position (l[j] = max(l[j-1], min(x, l[j]))) against six compare-selects
+// for a (value, index) pair.  Candidates are appended as (m, chunk) pairs
+// after one FP32 comparison, as in ChunkListF, and keyed in the merge, so
+// the per-step test costs the same in both lists.
+template <int MC, int BUFW>
+struct ChunkListK {
+  float* bv;
+  int* bi;
+  uint32_t* sk;
+  uint32_t hi;    // mask of the value bits
+  float qn;
+  uint32_t thr = 0xFFFFFFFFu;
+  // a chunk minimum m (d~ - ||q||^2) at or above thr_m cannot make a key
+  // below thr
+  float thr_m = FLT_MAX;
+  int cnt = 0;
+  __device__ void init() {
+#pragma unroll
+    for (int j = 0; j < MC; ++j) sk[j * 256] = 0xFFFFFFFFu;
+    thr = 0xFFFFFFFFu;
+    thr_m = FLT_MAX;
+    cnt = 0;
+  }
+  __device__ __forceinline__ void test(float m, int chunk) { chunk_test(m, chunk, thr_m, bv, bi, cnt); }
+  __device__ __forceinline__ bool full() const { return cnt > BUFW - 8; }
+  __device__ void flush() {
+    uint32_t l[MC];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) l[j] = sk[j * 256];
+    const int n = cnt;
+    const int nmax = __reduce_max_sync(kFull, n);
+    for (int s = 0; s < nmax; ++s) {
+      const uint32_t x =
+          s < n ? (f32_order_key(qn + bv[s * 256]) & hi) | (uint32_t)bi[s * 256] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int j = MC - 1; j > 0; --j) l[j] = max(l[j - 1], min(x, l[j]));
+      l[0] = min(x, l[0]);
+    }
+    thr = l[MC - 1];
+    cnt = 0;
+    // Keys below thr have value bits at most those of thr, so their d~ lies
+    // below U, the first value of the next key bucket; fl(qn + m) < U needs
+    // m < U - qn, which fl(U - qn) plus a few ulps of the operands bounds
+    // from above.
+    const uint32_t next = (thr & hi) + (~hi + 1u);
+    if (thr == 0xFFFFFFFFu || next < (thr & hi)) {
+      thr_m = FLT_MAX;
+    } else {
+      const float U = f32_from_order_key(next);
+      thr_m = (U - qn) + (fabsf(U) + fabsf(qn)) * 2.4e-7f;
+    }
+#pragma unroll
+    for (int j = 0; j < MC; ++j) sk[j * 256] = l[j];
+  }
+  __device__ void write(float, int64_t nd, float* od, int32_t* oi) const {
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      const uint32_t k = sk[j * 256];
+      const uint32_t c = k & ~hi;
+      const bool real = k != 0xFFFFFFFFu && (int64_t)c * 32 < nd;
+      od[j] = real ? f32_from_order_key(k & hi) : FLT_MAX;
+      oi[j] = real ? (int32_t)c : -1;
+    }
+  }
+};
+
 // kind::f16, D fp32, A and B of one type, K-major, M = 128, N = 256.
 __host__ __device__ constexpr uint32_t instr_desc_wide(uint32_t ab_type) {
   return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(TW_ROWS >> 3) << 17) |
          ((uint32_t)(TC_ROWS >> 4) << 24);
 }
 
-template <int KC, int MC, uint32_t AB_TYPE>
+template <int KC, int MC, uint32_t AB_TYPE, bool PACKED>
 __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
   constexpr uint32_t kATile = KC * TC_ROWS * 16;     // one 128-row query tile
   constexpr uint32_t kStep = KC * TW_ROWS * 16;      // one 256-row dictionary step
   constexpr int kKSteps = KC / 2;
   constexpr uint32_t kIdesc = instr_desc_wide(AB_TYPE);
-  constexpr int kStages = tw_stages(KC, MC);
-  constexpr int kBufW = 16;                          // append slots per epilogue lane
+  constexpr int kStages = tw_stages(KC, MC, PACKED);
+  constexpr int kBufW = tw_buf(PACKED);              // append slots per epilogue lane
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;                          // 2 query tiles
@@ -770,10 +917,9 @@ __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
   uint64_t* drain = acc_empty + 2;             // [2] one per issuing thread, at exit
   uint32_t* tmem_slot = (uint32_t*)(drain + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  float* buf_v = (float*)((unsigned char*)bars + kBarBytes);   // [kBufW][256]
-  int* buf_i = (int*)(buf_v + kBufW * 256);                      // [kBufW][256]
-  float* lst_v = (float*)(buf_i + kBufW * 256);                  // [MC][256]
-  int* lst_i = (int*)(lst_v + MC * 256);                         // [MC][256]
+  // epilogue: append buffers [kBufW][256] and lists [MC][256], one column
+  // per query row (values and indices, or keys)
+  unsigned char* epi = (unsigned char*)bars + kBarBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -894,10 +1040,21 @@ __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
     const int qt = ew >> 2;             // query tile
     const int quad = warp & 3;          // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;
-    float* bv = buf_v + ew * 32 + lane;
-    int* bi = buf_i + ew * 32 + lane;
-    float* sl_v = lst_v + ew * 32 + lane;
-    int* sl_i = lst_i + ew * 32 + lane;
+    const int col = ew * 32 + lane;     // this lane's column of the buffers and lists
+    using List = typename std::conditional<PACKED, ChunkListK<MC, kBufW>, ChunkListF<MC, kBufW>>::type;
+    List L;
+    float* bv = (float*)epi;
+    int* bi = (int*)(bv + kBufW * 256);
+    L.bv = bv + col;
+    L.bi = bi + col;
+    if constexpr (PACKED) {
+      L.sk = (uint32_t*)(bi + kBufW * 256) + col;
+      L.hi = ~((1u << a.id_bits) - 1u);
+    } else {
+      float* sv = (float*)(bi + kBufW * 256);
+      L.sv = sv + col;
+      L.si = (int*)(sv + MC * 256) + col;
+    }
     const bool releaser = quad == 0 && lane == 0;   // frees each step's ring stage (one per query tile)
     int stage = 0, item_no = 0;
     uint32_t accp = 0;
@@ -909,30 +1066,8 @@ __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
       const int64_t q = ((int64_t)qp * 2 + qt) * TC_ROWS + row;
       const bool valid = q < a.nq;
       const float qn = valid ? a.qn[q] : 0.f;
-      float ld[MC];
-      int li[MC];
-#pragma unroll
-      for (int j = 0; j < MC; ++j) {
-        ld[j] = FLT_MAX;
-        li[j] = -1;
-        sl_v[j * 256] = FLT_MAX;
-        sl_i[j * 256] = -1;
-      }
-      float thr = FLT_MAX;
-      int cnt = 0;
-      auto flush = [&]() {
-#pragma unroll
-        for (int j = 0; j < MC; ++j) {
-          ld[j] = sl_v[j * 256];
-          li[j] = sl_i[j * 256];
-        }
-        flush_appends<MC>(ld, li, thr, bv, bi, cnt);
-#pragma unroll
-        for (int j = 0; j < MC; ++j) {
-          sl_v[j * 256] = ld[j];
-          sl_i[j * 256] = li[j];
-        }
-      };
+      if constexpr (PACKED) L.qn = qn;
+      L.init();
       bool ok = true;
       for (int t = t0; t < t1; ++t) {
         const bool w = __all_sync(kFull, mbar_wait_fast(acc_full + qt, accp, abort_flag, a.status, a.wait_ns));
@@ -958,10 +1093,10 @@ __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
         tmem_ld32_min_issue(tb + 192, vc, m6);
         tmem_ld32_min_issue(tb + 224, vd, m7);
         const int c0 = t * 8;
-        chunk_test(m0, c0, thr, bv, bi, cnt);
-        chunk_test(m1, c0 + 1, thr, bv, bi, cnt);
-        chunk_test(m2, c0 + 2, thr, bv, bi, cnt);
-        chunk_test(m3, c0 + 3, thr, bv, bi, cnt);
+        L.test(m0, c0);
+        L.test(m1, c0 + 1);
+        L.test(m2, c0 + 2);
+        L.test(m3, c0 + 3);
         tmem_ld_wait(va, m4);
         tmem_regs_ready(vb, m5);
         tmem_regs_ready(vc, m6);
@@ -969,26 +1104,19 @@ __global__ void __launch_bounds__(352, 1) k_knn_tw(TcArgs a) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0 && (!withhold || t < t0 + 2)) mbar_arrive(acc_empty + qt);   // every read of it is done
-        chunk_test(m4, c0 + 4, thr, bv, bi, cnt);
-        chunk_test(m5, c0 + 5, thr, bv, bi, cnt);
-        chunk_test(m6, c0 + 6, thr, bv, bi, cnt);
-        chunk_test(m7, c0 + 7, thr, bv, bi, cnt);
+        L.test(m4, c0 + 4);
+        L.test(m5, c0 + 5);
+        L.test(m6, c0 + 6);
+        L.test(m7, c0 + 7);
         accp ^= 1u;
         if (++stage == kStages) stage = 0;
         // room for the next step's up to 8 appends in every lane
-        if (__any_sync(kFull, cnt > kBufW - 8)) flush();
+        if (__any_sync(kFull, L.full())) L.flush();
       }
       if (!ok) break;
-      flush();
+      L.flush();
       if (valid) {
-        float* od = a.out_d + ((int64_t)split * a.nq + q) * MC;
-        int32_t* oi = a.out_id + ((int64_t)split * a.nq + q) * MC;
-#pragma unroll
-        for (int j = 0; j < MC; ++j) {
-          const bool real = li[j] >= 0 && (int64_t)li[j] * 32 < a.nd;
-          od[j] = real ? qn + ld[j] : FLT_MAX;
-          oi[j] = real ? li[j] : -1;
-        }
+        L.write(qn, a.nd, a.out_d + ((int64_t)split * a.nq + q) * MC, a.out_id + ((int64_t)split * a.nq + q) * MC);
         if (a.tail_split > 0 && t0 == 0 && t1 == a.nd_tiles) {
           for (int s2 = 1; s2 < a.tail_split; ++s2) {
             float* od1 = a.out_d + ((int64_t)s2 * a.nq + q) * MC;
@@ -1577,16 +1705,17 @@ int tc_list_size(int precision, int K, int rerank_mult) {
   return rerank_mult * K <= 16 ? 16 : 32;
 }
 
-size_t tw_smem_bytes(int KC, int MC) {
-  return 1024 + (size_t)2 * KC * TC_ROWS * 16 + (size_t)tw_stages(KC, MC) * KC * TW_ROWS * 16 + kBarBytes +
-         (size_t)tw_epi_bytes(MC);
+size_t tw_smem_bytes(int KC, int MC, bool packed) {
+  return 1024 + (size_t)2 * KC * TC_ROWS * 16 + (size_t)tw_stages(KC, MC, packed) * KC * TW_ROWS * 16 +
+         kBarBytes + (size_t)tw_epi_bytes(MC, packed);
 }
 
 bool tc_wide_form(int precision, int kc) { return precision != 0 && (kc == 4 || kc == 8); }
 
-template <int KC, int MC, uint32_t T>
-static cudaError_t run_tw_kernel(const TcArgs& args, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_knn_tw<KC, MC, T>;
+template <int KC, int MC, uint32_t T, bool P>
+static cudaError_t run_tw_kernel(const TcArgs& args, int grid, cudaStream_t st) {
+  auto kern = k_knn_tw<KC, MC, T, P>;
+  const size_t smem = tw_smem_bytes(KC, MC, P);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
@@ -1640,9 +1769,18 @@ cudaError_t launch_knn_tc(const uint16_t* qop, const float* qn, int64_t nq, cons
     const int items = tail_split > 0 ? a.nq_pairs : a.nsplit * a.nq_pairs;
     grid = grid < items ? grid : items;
     a.full_rounds = tail_split > 0 ? a.nq_pairs / grid : 0;
-    const size_t smem = tw_smem_bytes(kc, MC);
+    // The BF16 form's 32-chunk lists are packed while the chunk numbers leave
+    // the keys at least 15 value bits (up to 2^17 chunks, 4,194,304 entries):
+    // there the merges dominate the list time (measured: 8 % off the filter
+    // with 1M entries, 2 % with 4M); 16-chunk lists merge rarely and run
+    // slightly faster unpacked.
+    a.id_bits = 3;
+    while ((int64_t{1} << a.id_bits) < (int64_t)a.nd_tiles * 8) ++a.id_bits;
+    const bool packed = precision == 1 && MC == 32 && a.id_bits <= 17;
 #define ZOOM_TW(KC, T) \
-  return MC == 16 ? run_tw_kernel<KC, 16, T>(a, grid, smem, st) : run_tw_kernel<KC, 32, T>(a, grid, smem, st)
+  return MC == 16 ? run_tw_kernel<KC, 16, T, false>(a, grid, st) : run_tw_kernel<KC, 32, T, false>(a, grid, st)
+    if (precision == 1 && kc == 4 && packed) return run_tw_kernel<4, 32, 1, true>(a, grid, st);
+    if (precision == 1 && kc == 8 && packed) return run_tw_kernel<8, 32, 1, true>(a, grid, st);
     if (precision == 2 && kc == 4) ZOOM_TW(4, 0);
     if (precision == 2 && kc == 8) ZOOM_TW(8, 0);
     if (precision == 1 && kc == 4) ZOOM_TW(4, 1);
