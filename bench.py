@@ -614,6 +614,18 @@ def run_single(a, wl, config, rank, world, local):
         if ms > 0:
             gbs = byts / (ms / 1e3) / 1e9
             kernels[name] = {"ms": ms, "algorithmic_bytes": byts, "GB/s": gbs, "frac_hbm": gbs / hbm_peak}
+    # the precision form's rerank: the search stage after its filter kernel (the SIMT re-run there has no
+    # queries).  Algorithmic bytes: the FP32 rows of the top 4K candidates gathered per query; the kernel
+    # reads whole 32-row chunks instead (from L2 mostly), about 8 of them per query
+    rr_ms = stage_bf.get("knn", 0.0) - stage_bf.get("knn_filter_kernel", 0.0)
+    if rr_ms > 0:
+        rr_bytes = nq * 4 * wl.K * wl.patch ** 2 * 4
+        gbs = rr_bytes / (rr_ms / 1e3) / 1e9
+        kernels["rerank"] = {"ms": rr_ms, "algorithmic_bytes": rr_bytes, "GB/s": gbs, "frac_hbm": gbs / hbm_peak,
+                             "kernels": f"k_rerank<{wl.patch ** 2},32>",
+                             "note": "algorithmic bytes: 4K rows of 4d bytes per query; the kernel stages "
+                                     "whole 32-entry chunks of 112-byte rows, about 8 per query (about 9x those bytes), mostly "
+                                     "from L2"}
     if "overlap_add" in kernels:
         kernels["overlap_add"]["kernels"] = "k_blend_rows + k_overlap_average"
         kernels["overlap_add"]["note"] = ("algorithmic bytes count every gathered HR residual value; repeated "
