@@ -624,8 +624,8 @@ def run_single(a, wl, config, rank, world, local):
         kernels["rerank"] = {"ms": rr_ms, "algorithmic_bytes": rr_bytes, "GB/s": gbs, "frac_hbm": gbs / hbm_peak,
                              "kernels": f"k_rerank<{wl.patch ** 2},32>",
                              "note": "algorithmic bytes: 4K rows of 4d bytes per query; the kernel stages "
-                                     "whole 32-entry chunks of 112-byte rows, about 8 per query (about 9x those bytes), mostly "
-                                     "from L2"}
+                                     "whole 32-entry chunks of 112-byte rows, about 8 per query (about 9x "
+                                     "those bytes), mostly from L2"}
     if "overlap_add" in kernels:
         kernels["overlap_add"]["kernels"] = "k_blend_rows + k_overlap_average"
         kernels["overlap_add"]["note"] = ("algorithmic bytes count every gathered HR residual value; repeated "
