@@ -167,44 +167,71 @@ struct Gauss1D {
   float c[16];
 };
 
-// The window radius is a template parameter: the clamped columns and their
-// LR columns are computed once per pixel (2R+1 divisions instead of
-// (2R+1)^2), in the same summation order as a direct double loop.
+// One block computes a 64-row x 32-column tile of x' from shared memory: the
+// tile of x with its R-pixel halo (clamped), then the separable sums -- each
+// row's box sum over the 2R+1 columns, and for each LR error row the
+// Gaussian-weighted sum over the 2R+1 replicated columns -- and per pixel the
+// column sums over 2R+1 rows.  The summation order is that of the direct
+// double loop (columns t within a row, then rows u), so the result is the
+// same bit for bit; x is read from memory once (with the halo) instead of
+// (2R+1)^2 times, and the LR row and column of every clamped tile row and
+// column are computed once per block.
+constexpr int kBpTileW = 32, kBpTileH = 64;
 template <int R>
-__global__ void k_bp_update(const float* __restrict__ x, float* __restrict__ xo, int H, int W,
-                            const float* __restrict__ e, int w, int s, Gauss1D g,
-                            float inv_two_sr2) {
-  const int X = blockIdx.x * blockDim.x + threadIdx.x;
-  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (X >= W || Y >= H) return;
+__global__ void __launch_bounds__(256) k_bp_update(const float* __restrict__ x, float* __restrict__ xo, int H,
+                                                   int W, const float* __restrict__ e, int w, int s, Gauss1D g,
+                                                   float inv_two_sr2) {
   constexpr int T = 2 * R + 1;
-  int cx[T], ce[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int xx = zoom_clampi(X + t - R, 0, W - 1);
-    cx[t] = xx;
-    ce[t] = xx / s;
+  constexpr int NW = kBpTileW + 2 * R, NH = kBpTileH + 2 * R;   // the tile with its halo
+  __shared__ float xs[NH][NW + 1];      // x, clamped
+  __shared__ float hs[NH][kBpTileW];    // row box sums
+  __shared__ float hg[NH][kBpTileW];    // per LR row: Gaussian row sums of the replicated error
+  __shared__ int lrow[NH], lcol[NW];    // LR row (relative to lr0) / column of each clamped tile row / column
+  const int X0 = blockIdx.x * kBpTileW, Y0 = blockIdx.y * kBpTileH;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lr0 = zoom_clampi(Y0 - R, 0, H - 1) / s;
+  const int nlr = zoom_clampi(Y0 + kBpTileH - 1 + R, 0, H - 1) / s - lr0 + 1;
+  for (int i = tid; i < NH; i += 256) lrow[i] = zoom_clampi(Y0 - R + i, 0, H - 1) / s - lr0;
+  for (int i = tid; i < NW; i += 256) lcol[i] = zoom_clampi(X0 - R + i, 0, W - 1) / s;
+  for (int i = tid; i < NH * NW; i += 256) {
+    const int r = i / NW, c = i % NW;
+    xs[r][c] = x[(int64_t)zoom_clampi(Y0 - R + r, 0, H - 1) * W + zoom_clampi(X0 - R + c, 0, W - 1)];
   }
-  float gs = 0.f, box = 0.f;
+  __syncthreads();
+  for (int i = tid; i < nlr * kBpTileW; i += 256) {
+    const int r = i / kBpTileW, c = i % kBpTileW;
+    const float* er = e + (int64_t)(lr0 + r) * w;
+    float grow = 0.f;
 #pragma unroll
-  for (int u = 0; u < T; ++u) {
-    const int yy = zoom_clampi(Y + u - R, 0, H - 1);
-    const float* xr = x + (int64_t)yy * W;
-    const float* er = e + (int64_t)(yy / s) * w;
-    float grow = 0.f, brow = 0.f;
+    for (int t = 0; t < T; ++t) grow = fmaf(g.c[t], er[lcol[c + t]], grow);
+    hg[r][c] = grow;
+  }
+  for (int i = tid; i < NH * kBpTileW; i += 256) {
+    const int r = i / kBpTileW, c = i % kBpTileW;
+    float brow = 0.f;
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-      grow = fmaf(g.c[t], er[ce[t]], grow);
-      brow += xr[cx[t]];
+    for (int t = 0; t < T; ++t) brow += xs[r][c + t];
+    hs[r][c] = brow;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  const int X = X0 + c;
+  if (X >= W) return;
+  for (int y = threadIdx.y; y < kBpTileH; y += blockDim.y) {
+    const int Y = Y0 + y;
+    if (Y >= H) break;
+    float gs = 0.f, box = 0.f;
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+      gs = fmaf(g.c[u], hg[lrow[y + u]][c], gs);
+      box += hs[y + u][c];
     }
-    gs = fmaf(g.c[u], grow, gs);
-    box += brow;
+    const float m = box / (float)(T * T);
+    const float xv = xs[y + R][c + R];
+    const float dv = xv - m;
+    const float r = expf(-dv * dv * inv_two_sr2);
+    xo[(int64_t)Y * W + X] = xv - r * gs;
   }
-  const float m = box / (float)((2 * R + 1) * (2 * R + 1));
-  const float xv = x[(int64_t)Y * W + X];
-  const float dv = xv - m;
-  const float r = expf(-dv * dv * inv_two_sr2);
-  xo[(int64_t)Y * W + X] = xv - r * gs;
 }
 
 }  // namespace
@@ -259,7 +286,7 @@ cudaError_t launch_bp_iteration(const float* x, float* x_out, const float* lr, f
   dim3 blk(32, 8);
   dim3 g1((w + 31) / 32, (h + 7) / 8);
   k_bp_error<<<g1, blk, 0, st>>>(x, H, W, lr, h, w, s, wt, err);
-  dim3 g2((W + 31) / 32, (H + 7) / 8);
+  dim3 g2((W + kBpTileW - 1) / kBpTileW, (H + kBpTileH - 1) / kBpTileH);
   const float inv = (float)(1.0 / (2.0 * (double)sigma_r * (double)sigma_r));
   switch (radius) {
 #define ZOOM_BPU(RR) \
