@@ -6,7 +6,9 @@ default bench line times, in both forms:
     form's recall of the oracle's neighbours on them;
   * every query of the exact form equal to the SIMT scan;
   * the BF16 form (the best 32 chunks reranked in FP32) against the exact
-    form over every query and every HR pixel: recall >= 0.99, PSNR >= 50 dB."""
+    form over every query and every HR pixel: recall >= 0.99, PSNR >= 50 dB;
+  * with a dictionary one entry past the packed list keys' limit, the BF16
+    form's unpacked 32-chunk lists against the exact form."""
 import os
 from concurrent.futures import ThreadPoolExecutor
 
@@ -102,3 +104,30 @@ def test_bf16_form_against_the_exact_form_3x(big):
     psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
     print(f"\nBF16 vs exact: recall {recall:.6f} over {ne.shape[0]} queries, PSNR {psnr:.1f} dB")
     assert psnr >= 50.0
+
+
+def test_bf16_32_chunk_lists_past_the_packed_key_limit(big):
+    # One entry past 4,194,304 the chunk numbers need 18 bits, more than the
+    # packed list keys leave room for: the BF16 form keeps its 32-chunk lists
+    # as (value, index) pairs there.  Same training images, a crop of the test
+    # image; recall of the exact form's neighbours.
+    Z, wl = big["Z"], big["wl"]
+    n = 4_194_305
+    lrs = wl.train_hr // wl.scale
+    pos = S.sample_positions(wl.pos_seed + 1, len(big["train"]), lrs, lrs, wl.patch, n)
+    d = Z.Dictionary(big["ctx"], [torch.from_numpy(x).cuda() for x in big["train"]], pos, wl.scale, wl.patch,
+                     wl.blur_sigma)
+    ix = Z.Index(d, wl.L, wl.k, wl.w, big["alpha"], big["beta"])
+    lr_c = big["lr_t"][:96, :160].contiguous()
+    q_ex = Z.query(ix, lr_c, G.params(wl))
+    q_bf = Z.query(ix, lr_c, G.params(wl, precision=1, rerank_mult=4))
+    scan = Z.query(ix, lr_c, G.params(wl, search=1))
+    big["ctx"].sync_status()
+    assert torch.equal(q_ex["nbr"], scan["nbr"]) and torch.equal(q_ex["dist"], scan["dist"])
+    ne, nb = q_ex["nbr"], q_bf["nbr"]
+    hits = sum((nb == ne[:, m:m + 1]).any(dim=1).int() for m in range(wl.K))
+    recall = float(hits.double().mean()) / wl.K
+    assert recall >= 0.99, recall
+    assert int(nb.min()) >= 0 and int(nb.max()) < n
+    ix.close()
+    d.close()
