@@ -165,9 +165,14 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
   h[threadIdx.x] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  // lanes of equal digit add their count once (digits of compacted ranks
+  // take few values, which would pile the atomics onto a few counters)
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
   for (int t = threadIdx.x; t < RS_TILE; t += RS_THREADS) {
     int64_t g = base + t;
-    if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255], 1);
+    const int digit = g < n ? (int)((keys[g] >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    if (digit < 256 && (peers & lt) == 0) atomicAdd(&h[digit], __popc(peers));
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -329,6 +334,173 @@ __global__ void k_csr_write(const uint64_t* __restrict__ keys, const int32_t* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// Key compaction for the bins (a3): a table of N entries holds few distinct
+// keys (68 to 661 per table with 1M pairs), so the 64-bit keys are replaced by
+// their rank among the table's distinct keys, and the stable sort by key
+// becomes a stable sort by a 12-bit rank: 2 radix passes of 8 bits instead
+// of 8.  Distinct keys go into a small open-addressing set per table (linear
+// probing, a slot claimed by a 64-bit compare-and-swap; the one key equal to
+// the empty marker is recorded by a flag); one block per table sorts them in
+// shared memory and gives every slot its rank.  A table with more distinct
+// keys than kKeySetCap keeps the 64-bit radix sort.
+// ---------------------------------------------------------------------------
+constexpr int kKeySetCap = 4096;            // distinct keys per table for the compacted sort
+constexpr int kKeySetSlots = 2 * kKeySetCap;
+constexpr uint64_t kEmptyKey = ~0ull;
+
+__device__ __forceinline__ uint32_t keyset_hash(uint64_t k) {
+  k ^= k >> 31;
+  k *= 0x7FB5D329728EA185ull;
+  return (uint32_t)(k >> 51) & (kKeySetSlots - 1);
+}
+
+// One thread per entry: its L keys (one 128-byte row) into the L sets.
+__global__ void k_keyset_insert(const uint64_t* __restrict__ dkeys, int64_t n, int L, uint64_t* slots,
+                                uint32_t* __restrict__ count, uint32_t* __restrict__ eflag,
+                                uint32_t* __restrict__ full) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int l = 0; l < L; ++l) {
+    const uint64_t key = dkeys[i * L + l];
+    if (key == kEmptyKey) {
+      if (atomicOr(eflag + l, 1u) == 0u) atomicAdd(count + l, 1u);
+      continue;
+    }
+    uint64_t* set = slots + (int64_t)l * kKeySetSlots;
+    uint32_t h = keyset_hash(key);
+    int p = 0;
+    for (; p < kKeySetSlots; ++p, h = (h + 1) & (kKeySetSlots - 1)) {
+      const uint64_t cur = *(volatile uint64_t*)(set + h);
+      if (cur == key) break;
+      if (cur == kEmptyKey) {
+        const unsigned long long old = atomicCAS((unsigned long long*)(set + h), (unsigned long long)kEmptyKey,
+                                                 (unsigned long long)key);
+        if (old == kEmptyKey) {
+          atomicAdd(count + l, 1u);
+          break;
+        }
+        if (old == key) break;
+      }
+    }
+    if (p == kKeySetSlots) atomicOr(full + l, 1u);   // no free slot left: the table keeps the 64-bit sort
+  }
+}
+
+// One block (1024 threads) per table with at most kKeySetCap distinct keys:
+// the set's keys sorted ascending (bitonic, in shared memory) into ukeys,
+// and the rank of each slot's key (and of the empty-marker key) recorded.
+__global__ void __launch_bounds__(1024) k_keyset_rank(const uint64_t* __restrict__ slots,
+                                                      const uint32_t* __restrict__ eflag,
+                                                      const uint32_t* __restrict__ compact, int64_t n,
+                                                      uint64_t* __restrict__ ukeys, int32_t* __restrict__ nuniq,
+                                                      uint16_t* __restrict__ slot_rank,
+                                                      uint16_t* __restrict__ erank) {
+  __shared__ uint64_t sk[kKeySetCap];
+  __shared__ uint16_t ss[kKeySetCap];   // slot of each key (kKeySetSlots: the empty-marker key)
+  __shared__ int m;
+  const int l = blockIdx.x;
+  if (!compact[l]) return;   // block-uniform
+  if (threadIdx.x == 0) m = 0;
+  __syncthreads();
+  const uint64_t* set = slots + (int64_t)l * kKeySetSlots;
+  for (int h = threadIdx.x; h < kKeySetSlots; h += blockDim.x) {
+    const uint64_t k = set[h];
+    if (k != kEmptyKey) {
+      const int j = atomicAdd(&m, 1);
+      sk[j] = k;
+      ss[j] = h;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && eflag[l]) {   // the empty-marker key is the largest of all
+    sk[m] = kEmptyKey;
+    ss[m] = kKeySetSlots;
+    ++m;
+  }
+  __syncthreads();
+  const int u = m;
+  int pw = 1;
+  while (pw < u) pw <<= 1;
+  for (int j = u + threadIdx.x; j < pw; j += blockDim.x) {   // padding sorts after every real key
+    sk[j] = kEmptyKey;
+    ss[j] = 0xFFFF;
+  }
+  __syncthreads();
+  for (int k = 2; k <= pw; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < pw; i += blockDim.x) {
+        const int o = i ^ j;
+        if (o > i) {
+          const bool up = (i & k) == 0;
+          const bool gt = sk[i] > sk[o] || (sk[i] == sk[o] && ss[i] > ss[o]);
+          if (gt == up) {
+            const uint64_t tk = sk[i];
+            sk[i] = sk[o];
+            sk[o] = tk;
+            const uint16_t ts = ss[i];
+            ss[i] = ss[o];
+            ss[o] = ts;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < u; r += blockDim.x) {
+    ukeys[(int64_t)l * n + r] = sk[r];
+    if (ss[r] < kKeySetSlots) slot_rank[(int64_t)l * kKeySetSlots + ss[r]] = (uint16_t)r;
+    else erank[l] = (uint16_t)r;
+  }
+  if (threadIdx.x == 0) nuniq[l] = u;
+}
+
+// One thread per entry: the rank of each of its keys in its table's set
+// (compacted tables only).
+__global__ void k_keyset_lookup(const uint64_t* __restrict__ dkeys, int64_t n, int L,
+                                const uint64_t* __restrict__ slots, const uint16_t* __restrict__ slot_rank,
+                                const uint16_t* __restrict__ erank, const uint32_t* __restrict__ compact,
+                                uint16_t* __restrict__ rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int l = 0; l < L; ++l) {
+    if (!compact[l]) continue;
+    const uint64_t key = dkeys[i * L + l];
+    uint16_t r = 0;
+    if (key == kEmptyKey) {
+      r = erank[l];
+    } else {
+      const uint64_t* set = slots + (int64_t)l * kKeySetSlots;
+      uint32_t h = keyset_hash(key);
+      for (int p = 0; p < kKeySetSlots; ++p, h = (h + 1) & (kKeySetSlots - 1)) {
+        if (set[h] == key) {
+          r = slot_rank[(int64_t)l * kKeySetSlots + h];
+          break;
+        }
+      }
+    }
+    rank[(int64_t)l * n + i] = r;
+  }
+}
+
+__global__ void k_rank_pairs(const uint16_t* __restrict__ rank, int64_t n, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ ids) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = rank[i];
+  ids[i] = (int32_t)i;
+}
+
+// Offsets of the runs of a rank-sorted table (its keys already written by
+// k_keyset_rank): a run starts where the rank changes, and the rank is the
+// run's index.
+__global__ void k_csr_rank_offsets(const uint64_t* __restrict__ r, int64_t n, int32_t* __restrict__ offs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i == 0 || r[i] != r[i - 1]) offs[r[i]] = (int32_t)i;
+  if (i == n - 1) offs[r[i] + 1] = (int32_t)n;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -451,10 +623,17 @@ size_t csr_scratch_bytes(int64_t n) {
   return (size_t)(2 * n * 8 + 2 * n * 4 + hist * 4 + 2 * n * 4 + nseg * 4 + 1024);
 }
 
+size_t csr_build_scratch_bytes(int64_t n, int L) {
+  // the radix sort's buffers, then the key sets, the slot ranks, the per-table
+  // flags and the 16-bit ranks of every entry in every table
+  return csr_scratch_bytes(n) + 256 + (size_t)L * kKeySetSlots * 8 + (size_t)L * kKeySetSlots * 2 +
+         (size_t)5 * L * 4 + 256 + (size_t)L * n * 2 + 256;
+}
+
 cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st) {
   const int64_t n = ix->dict->n;
   const int L = ix->L;
-  if (scratch_bytes < csr_scratch_bytes(n)) return cudaErrorInvalidValue;
+  if (scratch_bytes < csr_build_scratch_bytes(n, L)) return cudaErrorInvalidValue;
   const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
   char* p = (char*)scratch;
   uint64_t* ka = (uint64_t*)p; p += n * 8;
@@ -465,26 +644,81 @@ cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes,
   int32_t* head = (int32_t*)p; p += n * 4;
   int32_t* pos = (int32_t*)p; p += n * 4;
   int32_t* part = (int32_t*)p;
+  // compaction arrays after the radix sort's (csr_scratch_bytes(n) of them)
+  char* q = (char*)scratch + ((csr_scratch_bytes(n) + 255) & ~(size_t)255);
+  uint64_t* slots = (uint64_t*)q; q += (size_t)L * kKeySetSlots * 8;
+  uint16_t* slot_rank = (uint16_t*)q; q += (size_t)L * kKeySetSlots * 2;
+  uint32_t* flags = (uint32_t*)q; q += (size_t)5 * L * 4;   // count, eflag, full, compact, erank (16-bit)
+  uint32_t* count = flags;
+  uint32_t* eflag = flags + L;
+  uint32_t* full = flags + 2 * L;
+  uint32_t* compact = flags + 3 * L;
+  uint16_t* erank = (uint16_t*)(flags + 4 * L);
+  q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  uint16_t* rank = (uint16_t*)q;
   const int eb = (int)((n + 255) / 256);
+
+  // distinct keys per table; the host reads the counts (the build ends with
+  // a stream synchronisation anyway)
+  cudaError_t e = cudaMemsetAsync(slots, 0xFF, (size_t)L * kKeySetSlots * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, (size_t)5 * L * 4, st);
+  if (e != cudaSuccess) return e;
+  k_keyset_insert<<<eb, 256, 0, st>>>(ix->dkeys, n, L, slots, count, eflag, full);
+  std::vector<uint32_t> h_flags((size_t)3 * L);
+  e = cudaMemcpyAsync(h_flags.data(), flags, (size_t)3 * L * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  std::vector<uint32_t> h_compact(L);
+  bool any = false;
   for (int l = 0; l < L; ++l) {
-    k_extract_column<<<eb, 256, 0, st>>>(ix->dkeys, L, l, n, ka, va);
+    h_compact[l] = h_flags[2 * L + l] == 0 && h_flags[l] <= (uint32_t)kKeySetCap ? 1u : 0u;
+    any = any || h_compact[l];
+  }
+  if (any) {
+    e = cudaMemcpyAsync(compact, h_compact.data(), (size_t)L * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_keyset_rank<<<L, 1024, 0, st>>>(slots, eflag, compact, n, ix->ukeys, ix->nuniq, slot_rank, erank);
+    k_keyset_lookup<<<eb, 256, 0, st>>>(ix->dkeys, n, L, slots, slot_rank, erank, compact, rank);
+    // the copy of h_compact must finish before the vector goes
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int l = 0; l < L; ++l) {
     uint64_t* kin = ka; uint64_t* kout = kb;
     int32_t* vin = va; int32_t* vout = vb;
-    for (int shift = 0; shift < 64; shift += 8) {
-      k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
-      cudaError_t e = exclusive_scan(hist, hist, (int64_t)256 * ntiles, part, st);
+    if (h_compact[l]) {
+      // stable sort of the entries by their rank (below 4096): 2 passes of
+      // 8 bits, 1 when the table has at most 256 distinct keys
+      k_rank_pairs<<<eb, 256, 0, st>>>(rank + (int64_t)l * n, n, ka, va);
+      const int bits = h_flags[l] <= 256u ? 8 : 16;
+      for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+        e = exclusive_scan(hist, hist, (int64_t)256 * ntiles, part, st);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+      }
+      k_csr_rank_offsets<<<eb, 256, 0, st>>>(kin, n, ix->offs + (int64_t)l * (n + 1));
+    } else {
+      k_extract_column<<<eb, 256, 0, st>>>(ix->dkeys, L, l, n, ka, va);
+      for (int shift = 0; shift < 64; shift += 8) {
+        k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(kin, n, shift, hist, ntiles);
+        e = exclusive_scan(hist, hist, (int64_t)256 * ntiles, part, st);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+      }
+      k_csr_heads<<<eb, 256, 0, st>>>(kin, n, head);
+      e = exclusive_scan(head, pos, n, part, st);
       if (e != cudaSuccess) return e;
-      k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, hist, ntiles);
-      std::swap(kin, kout);
-      std::swap(vin, vout);
+      k_csr_write<<<eb, 256, 0, st>>>(kin, head, pos, n, ix->ukeys + (int64_t)l * n,
+                                      ix->offs + (int64_t)l * (n + 1), ix->nuniq + l);
     }
-    // after 8 passes the sorted data is back in ka / va
-    k_csr_heads<<<eb, 256, 0, st>>>(kin, n, head);
-    cudaError_t e = exclusive_scan(head, pos, n, part, st);
+    e = cudaMemcpyAsync(ix->ids + (int64_t)l * n, vin, n * 4, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    k_csr_write<<<eb, 256, 0, st>>>(kin, head, pos, n, ix->ukeys + (int64_t)l * n,
-                                    ix->offs + (int64_t)l * (n + 1), ix->nuniq + l);
-    cudaMemcpyAsync(ix->ids + (int64_t)l * n, vin, n * 4, cudaMemcpyDeviceToDevice, st);
   }
   return cudaGetLastError();
 }
+

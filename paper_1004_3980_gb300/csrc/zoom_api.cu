@@ -458,7 +458,7 @@ zoom_status zoom_build_index(zoom_dict d, const zoom_lsh_params* lsh, const floa
     e = launch_operand(d->feat, d->dpad, d->d, N, ix->nd_rows, 1, 2, ix->dopf1, nullptr, st);
   if (e == cudaSuccess) {
     Scratch scr(ctx, st);
-    size_t sb = csr_scratch_bytes(N);
+    size_t sb = csr_build_scratch_bytes(N, L);
     if (!scr.get(sb)) {
       rc = fail(ZOOM_ERR_OOM, "index build scratch");
     } else {

@@ -121,6 +121,8 @@ cudaError_t launch_hash(const float* feat, int dpad, int d, int64_t n, const flo
                         const float* beta, int L, int k, float w, uint64_t* keys, cudaStream_t st);
 cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t csr_scratch_bytes(int64_t n);
+// scratch of build_csr_tables: the radix sort's plus the key compaction's
+size_t csr_build_scratch_bytes(int64_t n, int L);
 
 // per-query steps (kernels_query.cu)
 // F: feature mode (0 pixels minus mean, 1 / 2 first / second-order gradients)
