@@ -1,6 +1,7 @@
 // Dictionary and LSH index construction (Sec. 2.1, Sec. 3.2, Sec. 4.1).
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "device_common.cuh"
@@ -491,6 +492,80 @@ __global__ void k_rank_pairs(const uint16_t* __restrict__ rank, int64_t n, uint6
   ids[i] = (int32_t)i;
 }
 
+// The same stable radix sort by rank for every table at once (blockIdx.y:
+// the table).  The histogram is laid out [table][digit][tile], so one
+// exclusive scan over all of it gives each item its position in the
+// concatenated [table][n] output: a table's items land after every earlier
+// table's n items.  ids_in == nullptr: the items' ids are their indices.
+__global__ void k_rank_hist_b(const uint16_t* __restrict__ r, int64_t n, int shift, int32_t* __restrict__ hist,
+                              int ntiles) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint16_t* rt = r + (int64_t)blockIdx.y * n;
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  for (int t = threadIdx.x; t < RS_TILE; t += RS_THREADS) {
+    const int64_t g = base + t;
+    const int digit = g < n ? (int)((rt[g] >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    if (digit < 256 && (peers & lt) == 0) atomicAdd(&h[digit], __popc(peers));
+  }
+  __syncthreads();
+  hist[((int64_t)blockIdx.y * 256 + threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_rank_scatter_b(const uint16_t* __restrict__ rin, const int32_t* __restrict__ ids_in,
+                                 uint16_t* __restrict__ rout, int32_t* __restrict__ ids_out, int64_t n, int shift,
+                                 const int32_t* __restrict__ offs, int ntiles) {
+  __shared__ int run[256];
+  __shared__ int wh[RS_THREADS / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t tb = (int64_t)blockIdx.y * n;   // this table's slice of the inputs
+  run[tid] = offs[((int64_t)blockIdx.y * 256 + tid) * ntiles + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < RS_TILE / RS_THREADS; ++c) {
+    const int64_t g = (int64_t)blockIdx.x * RS_TILE + c * RS_THREADS + tid;
+    const bool valid = g < n;
+    const uint16_t key = valid ? rin[tb + g] : 0;
+    const int32_t val = valid ? (ids_in ? ids_in[tb + g] : (int32_t)g) : 0;
+    const int digit = valid ? (int)((key >> shift) & 255) : 256;
+    for (int q = tid; q < (RS_THREADS / 32) * 256; q += RS_THREADS) (&wh[0][0])[q] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wh[warp][digit] = __popc(peers);
+    __syncthreads();
+    {
+      int sacc = run[tid];
+#pragma unroll
+      for (int q = 0; q < RS_THREADS / 32; ++q) {
+        const int t = wh[q][tid];
+        wh[q][tid] = sacc;
+        sacc += t;
+      }
+      run[tid] = sacc;
+    }
+    __syncthreads();
+    if (valid) {
+      const int64_t pos = (int64_t)wh[warp][digit] + rank;
+      rout[pos] = key;
+      ids_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// Bin offsets of every table from its rank-sorted ranks (blockIdx.y: table).
+__global__ void k_csr_rank_offsets_b(const uint16_t* __restrict__ r, int64_t n, int32_t* __restrict__ offs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint16_t* rt = r + (int64_t)blockIdx.y * n;
+  int32_t* ot = offs + (int64_t)blockIdx.y * (n + 1);
+  if (i == 0 || rt[i] != rt[i - 1]) ot[rt[i]] = (int32_t)i;
+  if (i == n - 1) ot[rt[i] + 1] = (int32_t)n;
+}
+
 // Offsets of the runs of a rank-sorted table (its keys already written by
 // k_keyset_rank): a run starts where the rank changes, and the rank is the
 // run's index.
@@ -625,9 +700,13 @@ size_t csr_scratch_bytes(int64_t n) {
 
 size_t csr_build_scratch_bytes(int64_t n, int L) {
   // the radix sort's buffers, then the key sets, the slot ranks, the per-table
-  // flags and the 16-bit ranks of every entry in every table
+  // flags, the 16-bit ranks of every entry in every table (twice) and their
+  // ids, and the all-table histogram with its scan partials
+  const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t hist = (int64_t)L * 256 * ntiles;
   return csr_scratch_bytes(n) + 256 + (size_t)L * kKeySetSlots * 8 + (size_t)L * kKeySetSlots * 2 +
-         (size_t)5 * L * 4 + 256 + (size_t)L * n * 2 + 256;
+         (size_t)5 * L * 4 + 256 + (size_t)L * n * 2 + 256 + (size_t)L * n * 2 + 256 + (size_t)L * n * 4 + 256 +
+         (size_t)hist * 4 + 256 + (size_t)((hist + SCAN_SEG - 1) / SCAN_SEG) * 4 + 1024;
 }
 
 cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes, cudaStream_t st) {
@@ -655,7 +734,15 @@ cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes,
   uint32_t* compact = flags + 3 * L;
   uint16_t* erank = (uint16_t*)(flags + 4 * L);
   q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
-  uint16_t* rank = (uint16_t*)q;
+  uint16_t* rank = (uint16_t*)q; q += (size_t)L * n * 2;
+  q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  uint16_t* rank_b = (uint16_t*)q; q += (size_t)L * n * 2;
+  q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  int32_t* ids_b = (int32_t*)q; q += (size_t)L * n * 4;
+  q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  int32_t* hist_b = (int32_t*)q; q += (size_t)L * 256 * ntiles * 4;
+  q = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  int32_t* part_b = (int32_t*)q;
   const int eb = (int)((n + 255) / 256);
 
   // distinct keys per table; the host reads the counts (the build ends with
@@ -682,6 +769,33 @@ cudaError_t build_csr_tables(zoom_index ix, void* scratch, size_t scratch_bytes,
     // the copy of h_compact must finish before the vector goes
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
+  }
+  bool all = true;
+  uint32_t umax = 0;
+  for (int l = 0; l < L; ++l) {
+    all = all && h_compact[l];
+    umax = std::max(umax, h_flags[l]);
+  }
+  if (all && (int64_t)L * n < (int64_t{1} << 31)) {   // positions in 32-bit scans
+    // every table at once: 1 pass of 8 bits when no table has more than 256
+    // distinct keys, else 2; the last pass writes the ids into the index
+    const int passes = umax <= 256u ? 1 : 2;
+    const dim3 grid(ntiles, L);
+    const uint16_t* rin = rank;
+    uint16_t* rout = rank_b;
+    const int32_t* iin = nullptr;
+    for (int ps = 0; ps < passes; ++ps) {
+      int32_t* iout = ps == passes - 1 ? ix->ids : ids_b;
+      k_rank_hist_b<<<grid, RS_THREADS, 0, st>>>(rin, n, 8 * ps, hist_b, ntiles);
+      e = exclusive_scan(hist_b, hist_b, (int64_t)L * 256 * ntiles, part_b, st);
+      if (e != cudaSuccess) return e;
+      k_rank_scatter_b<<<grid, RS_THREADS, 0, st>>>(rin, iin, rout, iout, n, 8 * ps, hist_b, ntiles);
+      iin = iout;
+      rin = rout;
+      rout = rout == rank_b ? rank : rank_b;
+    }
+    k_csr_rank_offsets_b<<<dim3(eb, L), 256, 0, st>>>(rin, n, ix->offs);
+    return cudaGetLastError();
   }
   for (int l = 0; l < L; ++l) {
     uint64_t* kin = ka; uint64_t* kout = kb;
