@@ -868,10 +868,10 @@ struct ChunkListK {
     // m < U - qn, which fl(U - qn) plus a few ulps of the operands bounds
     // from above.
     const uint32_t next = (thr & hi) + (~hi + 1u);
-    if (thr == 0xFFFFFFFFu || next < (thr & hi)) {
-      thr_m = FLT_MAX;
+    const float U = f32_from_order_key(next);
+    if (thr == 0xFFFFFFFFu || next < (thr & hi) || !(U < FLT_MAX)) {
+      thr_m = FLT_MAX;   // no bound below infinity (or the list is not full): test nothing away
     } else {
-      const float U = f32_from_order_key(next);
       thr_m = (U - qn) + (fabsf(U) + fabsf(qn)) * 2.4e-7f;
     }
 #pragma unroll
